@@ -1,0 +1,140 @@
+"""Pins for the oracle's AF-IETI (Section 4, Section 5.2, Remark 1): the
+constraint count against dim of the conforming space, full row rank and the
+block-diagonal B B^T, the projector identities, lambda_0, the iterative
+solution against the conforming direct solve (the unique solution of
+eq. 4.2), vanishing jumps, the monotone MINRES estimate and MINRES against a
+dense solve; plus the adjoint gradients against central finite differences."""
+import numpy as np
+import pytest
+
+import afi_workloads as W
+from oracle import adjoint
+from oracle.ieti import AFIETI
+from oracle.minres import minres
+
+
+@pytest.fixture(scope="module")
+def c1():
+    P = W.config("C1")
+    s = AFIETI(P)
+    f = s.load(W.body_force_coeffs(P))
+    return P, s, f
+
+
+@pytest.fixture(scope="module")
+def c2s():
+    P = W.config("C2-small")
+    s = AFIETI(P)
+    f = s.load(W.body_force_coeffs(P))
+    return P, s, f
+
+
+def test_constraint_counts(c1, c2s):
+    for P, s, _ in (c1, c2s):
+        Z = s.conforming_basis()
+        assert s.nc == s.ndof - Z.shape[1]
+    assert c1[1].nc == 222                     # 152 Dirichlet + 64 edge + 6 cross-point rows
+
+
+def test_B_rank_and_BBt_blocks(c1):
+    _, s, _ = c1
+    Bd = s.B.toarray()
+    assert np.linalg.matrix_rank(Bd) == s.nc
+    BBt = s.BBt.toarray()
+    seen = np.zeros(s.nc, dtype=bool)
+    for c, n, ids in s.node_rows:
+        if not ids:
+            continue
+        blk = BBt[np.ix_(ids, ids)]
+        m = len(ids)
+        ref = np.eye(m) if s.dirichlet[n] else np.eye(m) + np.ones((m, m))
+        np.testing.assert_array_equal(blk, ref)
+        seen[ids] = True
+        others = np.setdiff1d(np.arange(s.nc), ids)
+        assert not BBt[np.ix_(ids, others)].any()
+    assert seen.all()
+
+
+def test_projectors(c2s):
+    _, s, f = c2s
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(s.nc)
+    y = rng.standard_normal(s.nc)
+    px = s.P_chi(x)
+    np.testing.assert_allclose(s.P_chi(px), px, atol=1e-10)
+    np.testing.assert_allclose(s.G.T @ px, 0.0, atol=1e-10)
+    assert abs(px @ y - x @ s.P_chi(y)) < 1e-9
+    Rd = s.R.toarray()
+    for j in range(0, Rd.shape[1], 5):
+        np.testing.assert_allclose(s.P_u(Rd[:, j]), 0.0, atol=1e-11)
+    lam0 = s.lambda0(f)
+    np.testing.assert_allclose(s.G.T @ lam0, s.R.T @ f, atol=1e-11)
+
+
+@pytest.mark.parametrize("which", ["c1", "c2s"])
+def test_afieti_equals_direct(which, request):
+    _, s, f = request.getfixturevalue(which)
+    u, lam, info = s.solve(f, tol=1e-8)
+    ud, ld = s.direct_solve(f)
+    assert info["true_relres"] <= 1e-8
+    assert np.linalg.norm(u - ud) <= 1e-6 * np.linalg.norm(ud)
+    assert np.linalg.norm(lam - ld) <= 1e-6 * np.linalg.norm(ld)
+    assert np.linalg.norm(s.B @ u) <= 1e-8 * np.linalg.norm(u)
+    h = np.array(info["history"])
+    assert (np.diff(h) <= 1e-12).all()        # MINRES residual estimate is monotone
+
+
+def test_preconditioner_spd_on_subspace():
+    P = W.config("C1-small")
+    s = AFIETI(P)
+    n, m = s.ndof, s.nc
+    # basis of range(A) x ker(G^T) through the projectors
+    E = np.eye(n + m)
+    M = np.stack([np.concatenate(s.precond_apply(E[i, :n], E[i, n:])) for i in range(n + m)], axis=1)
+    np.testing.assert_allclose(M, M.T, atol=1e-9 * abs(M).max())
+    ev = np.linalg.eigvalsh(0.5 * (M + M.T))
+    assert ev.min() > -1e-9 * ev.max()
+
+
+def test_minres_matches_dense_solve():
+    rng = np.random.default_rng(11)
+    n = 60
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = Q @ np.diag(np.concatenate([rng.uniform(1, 5, 40), -rng.uniform(1, 5, 20)])) @ Q.T
+    L = rng.standard_normal((n, n)) / np.sqrt(n)
+    Minv = L @ L.T + np.eye(n)
+    b = rng.standard_normal(n)
+    x, info = minres(lambda v: A @ v, b, lambda v: Minv @ v, tol=1e-12, maxit=500)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-10)
+    assert (np.diff(info["history"]) <= 1e-14).all()
+
+
+def test_adjoint_gradients_vs_finite_differences():
+    P = W.config("C1-small")
+    P.lame = P.lame * np.array([[1.0, 1.0], [1.3, 0.8], [0.7, 1.1], [1.0, 1.2]])
+    s = AFIETI(P)
+    f = s.load(W.body_force_coeffs(P))
+    J, dJdf, dJdlame = adjoint.compliance_and_grads(s, f)
+    u, _, _ = s.solve(f, tol=1e-12)
+    J_it, _, g_it = adjoint.compliance_and_grads(s, f, direct=False)
+    np.testing.assert_allclose(g_it, dJdlame, rtol=1e-7)
+    h = 1e-6
+    for k in range(P.npatch):
+        for j in range(2):
+            vals = []
+            for sgn in (1, -1):
+                P2 = W.config("C1-small")
+                P2.lame = P.lame.copy()
+                P2.lame[k, j] += sgn * h
+                s2 = AFIETI(P2)
+                u2, _ = s2.direct_solve(f)
+                vals.append(f @ u2)
+            fdg = (vals[0] - vals[1]) / (2 * h)
+            assert abs(fdg - dJdlame[k, j]) <= 1e-5 * max(abs(fdg), 1e-12), (k, j, fdg, dJdlame[k, j])
+    rng = np.random.default_rng(2)
+    for i in rng.choice(s.ndof, 5, replace=False):
+        e = np.zeros(s.ndof); e[i] = h
+        up, _ = s.direct_solve(f + e)
+        um, _ = s.direct_solve(f - e)
+        fdg = ((f + e) @ up - (f - e) @ um) / (2 * h)
+        assert abs(fdg - dJdf[i]) <= 1e-5 * max(abs(fdg), 1e-8)
