@@ -1,0 +1,192 @@
+/*
+ * afieti.h - C ABI of the GB300 (sm_103a) inexact All-Floating IETI solver for
+ * multi-patch isogeometric compressible linear elasticity
+ * (Bosy, Montardini, Sangalli, Tani, arXiv 2001.09626).
+ *
+ * The library solves the saddle-point system of eq. (4.5),
+ *     [A B^T; B 0] [u; lambda] = [f; 0],
+ * by MINRES on the projected system of eq. (4.7) preconditioned by the
+ * block-diagonal operator of eq. (4.9) with the inexact local solvers of
+ * Section 5.2 (fast diagonalization, Algorithm 1) and the non-redundant
+ * Schur-type multiplier preconditioner of Remark 1.
+ *
+ * Conventions shared by every entry point
+ *  - "torn" vectors (length n_dof): patches stacked in input order; inside a
+ *    patch the d displacement components are stacked; each component is an
+ *    n3*n2*n1 block in colexicographic order, i1 fastest (Section 2.2).
+ *  - multiplier vectors (length n_c): one entry per row of B, rows ordered
+ *    component-major, then by geometric node (nodes ordered by their first
+ *    copy (patch, local index)); a node on the Dirichlet boundary has one row
+ *    per copy, any other node has rows u_{c1} - u_{cj}, j = 2..m.
+ *  - every *_dev pointer is device memory of the current CUDA device, FP64,
+ *    contiguous, owned by the caller; with nrhs > 1 vectors are stacked
+ *    [nrhs][length].  Host pointers (afi_problem fields) are read during the
+ *    call and not retained.
+ *  - the context owns all setup data and workspaces; one context may be used
+ *    by one host thread and one stream at a time.
+ *  - errors are reported through the returned status, never by aborting;
+ *    afi_last_error() gives a message for the most recent failure.
+ */
+#ifndef AFIETI_H
+#define AFIETI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AFI_OK = 0,
+  AFI_EINVAL = 1,          /* invalid argument or geometry (e.g. det J <= 0) */
+  AFI_ENOMEM = 2,          /* device allocation failed */
+  AFI_ECUDA = 3,           /* a CUDA runtime call failed */
+  AFI_ESINGULAR = 4,       /* G^T G or a pencil is not positive definite */
+  AFI_ENOT_CONVERGED = 5,  /* maxit reached before the tolerance */
+  AFI_EBREAKDOWN = 6,      /* MINRES breakdown (non-finite or negative norm) */
+  AFI_ETIMEOUT = 7
+} afi_status;
+
+/* Arithmetic of the local solvers (fast diagonalization and the parametric
+ * stiffness products inside the Schur preconditioner).  Everything else
+ * (stiffness matvec, jumps, projectors, Krylov algebra) is FP64 always. */
+typedef enum {
+  AFI_FD_FP64 = 0,   /* plain form: FP64 throughout */
+  AFI_FD_FP32 = 1,   /* FP32 contractions, FP32 accumulate */
+  AFI_FD_TF32 = 2,   /* TF32 tensor-core contractions, FP32 accumulate */
+  AFI_FD_BF16 = 3    /* BF16 tensor-core contractions, FP32 accumulate */
+} afi_fd_precision;
+
+typedef struct afi_ctx afi_ctx;   /* opaque, owned by the library */
+
+/* Problem description (Sections 2-4), host memory.
+ *   dim            2 or 3
+ *   npatch         number of patches
+ *   degree[k]      spline degree of patch k (same in every direction)
+ *   nel[k*dim+l]   elements of patch k in direction l: open uniform knot
+ *                  vector with single interior knots (C^{p-1} splines),
+ *                  n_l = nel + degree basis functions
+ *   ctrl           control points of all patches concatenated, each patch
+ *                  [i3][i2][i1][dim] (i1 fastest); the geometry map is the
+ *                  isoparametric spline map of Section 2.2.  Shared interface
+ *                  control points must coincide (conforming patches); they
+ *                  are matched by coordinates (relative tolerance 1e-10)
+ *   lame[2k+0,1]   (lambda_k, mu_k) of patch k (eq. 3.1)
+ *   dirichlet_face[k*2*dim + 2*l + side]  1 if the face eta_l = side of
+ *                  patch k carries the homogeneous Dirichlet condition      */
+typedef struct {
+  int dim, npatch;
+  const int *degree;
+  const int *nel;
+  const double *ctrl;
+  const double *lame;
+  const unsigned char *dirichlet_face;
+} afi_problem;
+
+/* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
+ * preconditioned residual estimate and then the true FP64 residual
+ * ||b - A x|| / ||b|| of eq. (4.7) must both reach it); maxit: iteration cap;
+ * use_graph, variant: reserved, pass 0. */
+typedef struct {
+  afi_fd_precision prec;
+  double tol;
+  int maxit;
+  int use_graph;
+  int variant;
+} afi_options;
+
+/* Filled by ieti_solve / ieti_solve_adjoint (for the last right-hand side):
+ * iterations, the MINRES estimate, the true relative residual, the setup
+ * time of the context and the wall time of this solve (device events). */
+typedef struct {
+  int iters;
+  double relres_est, relres_true;
+  double t_setup_ms, t_solve_ms;
+} afi_info;
+
+/* Operators of the hot path, for afi_apply (each is one row of the solve):
+ *  AFI_OP_STIFFNESS  y = A x                 (torn -> torn), eqs. 3.1, 4.2
+ *  AFI_OP_B          y = B x                 (torn -> multipliers), Sec. 4
+ *  AFI_OP_BT         y = B^T x               (multipliers -> torn)
+ *  AFI_OP_PCHI       y = P_chi x             (multipliers), eq. 4.6
+ *  AFI_OP_PU         y = P_u x               (torn), Sec. 4 after eq. 4.9
+ *  AFI_OP_PA_INV     y = P_A^{-1} x          (torn), eq. 5.6 by Algorithm 1
+ *  AFI_OP_SCHUR      y = blkdiag H^{d-2} S_hat x (torn shell -> torn shell),
+ *                    eqs. 5.4-5.5; interior entries of y are written as zero
+ *  AFI_OP_PS         y = (B B^T)^{-1} B S_hat_H B^T (B B^T)^{-1} x  (Remark 1)
+ *  AFI_OP_PRECOND    y = calB^{-1} x         ([torn; multipliers]), eq. 4.9
+ *  AFI_OP_SADDLE     y = calA x              ([torn; multipliers]), eq. 4.7 */
+typedef enum {
+  AFI_OP_STIFFNESS = 0, AFI_OP_B = 1, AFI_OP_BT = 2, AFI_OP_PCHI = 3,
+  AFI_OP_PU = 4, AFI_OP_PA_INV = 5, AFI_OP_SCHUR = 6, AFI_OP_PS = 7,
+  AFI_OP_PRECOND = 8, AFI_OP_SADDLE = 9
+} afi_operator;
+
+/* Setup (Section 2.1 knots and B-splines, Section 4 constraints, rigid modes
+ * and G^T G, Section 5.2.1 step 1 generalised eigendecompositions, and the
+ * assembly of every patch stiffness A^(k) by Gauss quadrature with p+1
+ * points per element and direction).  Runs on the current device, returns
+ * after the work is complete.  *out receives a new context on success.
+ * Errors: AFI_EINVAL (bad sizes, non-conforming interfaces, det J <= 0),
+ * AFI_ESINGULAR (G^T G not positive definite), AFI_ENOMEM, AFI_ECUDA. */
+afi_status af_ieti_setup(const afi_problem *prob, const afi_options *opt, afi_ctx **out);
+
+/* Algorithm 1 (steps 2-4) on every (patch, component) block:
+ *  interior = 0: s = P_A^{inex,-1} r = blkdiag [H^{d-2}(A_hat_l + M_hat_l)]^{-1} r
+ *               over torn vectors (eqs. 5.6, 5.9);
+ *  interior = 1: s = (A_hat_l)_II^{-1} r over the compact interior blocks
+ *               (each block (n3-2)(n2-2)(n1-2), i1 fastest, patches and
+ *               components stacked like torn vectors; eq. 5.10).
+ * Uses the context's precision.  Stream-ordered, asynchronous. */
+afi_status fd_apply(afi_ctx *ctx, int interior, const double *r_dev, double *s_dev,
+                    int nrhs, void *stream);
+
+/* AF-IETI solve: lambda_0 = G (G^T G)^{-1} R^T f, MINRES on eq. (4.7) from a
+ * zero guess, recovery u = w - R (G^T G)^{-1} G^T B w, lambda = lambda_0 + chi
+ * (Section 4).  f_dev, u_dev: [nrhs][n_dof]; lambda_dev: [nrhs][n_c] or NULL.
+ * The call returns when the solve has finished (the host polls the
+ * convergence flag).  info may be NULL.  Returns AFI_ENOT_CONVERGED if maxit
+ * was reached (u is still the last iterate's recovery). */
+afi_status ieti_solve(afi_ctx *ctx, const double *f_dev, double *u_dev, double *lambda_dev,
+                      int nrhs, afi_info *info, void *stream);
+
+/* Adjoint solve.  The saddle matrix of eq. (4.5) is symmetric, so the
+ * adjoint state (z, z_lambda) for an objective gradient g = dJ/du solves the
+ * same system with right-hand side g.  Same layout and errors as ieti_solve.
+ * (The paper has no differentiation; this entry point extends it.) */
+afi_status ieti_solve_adjoint(afi_ctx *ctx, const double *g_dev, double *z_dev,
+                              double *zlambda_dev, int nrhs, afi_info *info, void *stream);
+
+/* Gradient with respect to the Lame values: A^(k) is linear in
+ * (lambda_k, mu_k) (eq. 3.1), so dJ/dlambda_k = -z_k^T A_lambda^(k) u_k and
+ * dJ/dmu_k = -z_k^T A_mu^(k) u_k, with A_lambda = int div div and
+ * A_mu = int 2 eps:eps.  grad_dev: [npatch][2] (lambda, mu).  For the
+ * compliance J = f^T u pass z = u. */
+afi_status afi_lame_grad(afi_ctx *ctx, const double *u_dev, const double *z_dev,
+                         double *grad_dev, void *stream);
+
+/* Load vector of a body force with nodal coefficients c (torn layout):
+ * f^(k) = M^(k) c^(k), M^(k) the mapped mass matrix of eq. (4.8). */
+afi_status afi_load_vector(afi_ctx *ctx, const double *c_dev, double *f_dev, void *stream);
+
+/* One hot-path operator (see afi_operator) applied to x_dev, result in
+ * y_dev (lengths as listed there).  Stream-ordered, asynchronous. */
+afi_status afi_apply(afi_ctx *ctx, afi_operator op, const double *x_dev, double *y_dev,
+                     void *stream);
+
+/* Change the local-solver arithmetic of an existing context (the low
+ * precision copies of the eigenvectors are built at setup). */
+afi_status afi_set_precision(afi_ctx *ctx, afi_fd_precision prec);
+
+/* n_dof (torn length) and n_c (number of constraints). */
+afi_status afi_sizes(const afi_ctx *ctx, long *n_dof, long *n_c);
+
+/* Device bytes held by the context and the stiffness storage alone. */
+afi_status afi_memory(const afi_ctx *ctx, long long *total_bytes, long long *stiffness_bytes);
+
+void af_ieti_destroy(afi_ctx *ctx);
+const char *afi_status_string(afi_status s);
+const char *afi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFIETI_H */

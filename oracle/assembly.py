@@ -144,7 +144,7 @@ def stiffness_parts(g: PatchGeometry, qr=None, cr=None):
 
 
 def mass_block(g: PatchGeometry, qr=None, cr=None):
-    """Scalar mapped mass M_ij = int B_i B_j dx (each component block, eq. 4.5)."""
+    """Scalar mapped mass M_ij = int B_i B_j dx (each component block, eq. 4.8)."""
     qr = g.full_q() if qr is None else qr
     cr = g.full_c() if cr is None else cr
     Phi0, Phis, w, cols, det, Q = _geometry_block(g, qr, cr)

@@ -15,7 +15,7 @@ from . import spline
 
 
 def gen_eig(K: np.ndarray, M: np.ndarray):
-    """Generalised eigendecomposition (eq. 5.6): U^T K U = D, U^T M U = I.
+    """Generalised eigendecomposition (eq. 5.8): U^T K U = D, U^T M U = I.
     LAPACK sygv through scipy.linalg.eigh (library step)."""
     D, U = sla.eigh(K, M)
     return D, U
@@ -34,7 +34,7 @@ def coeffs(dim: int, l: int, lam: float, mu: float) -> list:
 
 
 def Lambda(D: list, dim: int, l: int, lam: float, mu: float, H: float) -> np.ndarray:
-    """Diagonal of Lambda_l (eq. 5.7), shaped [n_d, ..., n_1]:
+    """Diagonal of Lambda_l (eq. 5.9), shaped [n_d, ..., n_1]:
     H^{d-2} (sum_j c_j D_j + 1)."""
     c = coeffs(dim, l, lam, mu)
     out = np.ones([len(D[j]) for j in reversed(range(dim))])
@@ -46,7 +46,7 @@ def Lambda(D: list, dim: int, l: int, lam: float, mu: float, H: float) -> np.nda
 
 
 def Lambda_interior(Dt: list, dim: int, l: int, lam: float, mu: float) -> np.ndarray:
-    """Diagonal of Lambda~_l (eq. 5.8): sum_j c_j D~_j (no mass, no H factor)."""
+    """Diagonal of Lambda~_l (eq. 5.10): sum_j c_j D~_j (no mass, no H factor)."""
     c = coeffs(dim, l, lam, mu)
     out = np.zeros([len(Dt[j]) for j in reversed(range(dim))])
     for j in range(dim):

@@ -4,7 +4,7 @@ direct solve that defines the exact answer.  Oracle code: test infrastructure
 only.
 
 Readings where the paper is silent (each listed in the design notes):
-  * B (eq. 4.2 assumption ker B^T = 0): per component and per geometric node
+  * B (Section 4, assumption ker B^T = 0): per component and per geometric node
     with copies c_1 < ... < c_m (ordered by (patch, local index)): a node on
     the Dirichlet boundary gets one row e_{c_j} per copy; any other node gets
     the star rows u_{c_1} - u_{c_j}, j = 2..m.  Rows are component-major, then
@@ -157,7 +157,7 @@ class AFIETI:
                                for k, g in enumerate(self.geo)])
 
     def P_chi(self, x):
-        """Orthogonal projection onto ker(G^T) (eq. 4.3)."""
+        """Orthogonal projection onto ker(G^T) (eq. 4.6)."""
         return x - self.G @ np.linalg.solve(self.GtG, self.G.T @ x)
 
     def P_u(self, v):
@@ -192,7 +192,7 @@ class AFIETI:
         return loc
 
     def PA_inv(self, r):
-        """blkdiag_k,l [H^{d-2}(A_hat_l + M_hat_l)]^{-1} (eq. 5.4) by sparse LU."""
+        """blkdiag_k,l [H^{d-2}(A_hat_l + M_hat_l)]^{-1} (eq. 5.6) by sparse LU."""
         out = np.empty_like(r)
         for k, (per, mask, Hs) in enumerate(self._local()):
             for l in range(self.dim):
@@ -202,7 +202,7 @@ class AFIETI:
 
     def S_hat_H(self, t):
         """blkdiag_k H_k^{d-2} S_hat^(k) on a torn vector supported on the shell
-        (eq. 5.5 / 5.3): S theta = A_GG theta - A_GI A_II^{-1} A_IG theta."""
+        (eqs. 5.4-5.5, 5.7): S theta = A_GG theta - A_GI A_II^{-1} A_IG theta."""
         out = np.zeros_like(t)
         for k, (per, mask, Hs) in enumerate(self._local()):
             for l in range(self.dim):
@@ -223,7 +223,7 @@ class AFIETI:
         return self.BBt_lu.solve(y)
 
     def precond_apply(self, rw, rc):
-        """B^{-1} of eq. 4.6: blkdiag(P_u P_A^{-1} P_u^T, P_chi P_S P_chi^T)."""
+        """B^{-1} of eq. 4.9: blkdiag(P_u P_A^{-1} P_u^T, P_chi P_S P_chi^T)."""
         zw = self.P_u(self.PA_inv(self.P_u(rw)))
         zc = self.P_chi(self.P_S(self.P_chi(rc)))
         return zw, zc
@@ -232,7 +232,7 @@ class AFIETI:
         return self.G @ np.linalg.solve(self.GtG, self.R.T @ f)
 
     def op(self, w, chi):
-        """The projected saddle operator of eq. 4.4."""
+        """The projected saddle operator of eq. 4.7."""
         A = self.assemble()
         pc = self.P_chi(chi)
         return A @ w + self.B.T @ pc, self.P_chi(self.B @ w)

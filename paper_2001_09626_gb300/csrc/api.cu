@@ -1,0 +1,134 @@
+// extern "C" entry points declared in include/afieti.h.
+#include "common.cuh"
+
+namespace afi {
+const char *last_error_cstr();
+}
+
+using namespace afi;
+
+static cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+afi_status af_ieti_setup(const afi_problem *prob, const afi_options *opt, afi_ctx **out) {
+  if (!out) { set_error("out is null"); return AFI_EINVAL; }
+  *out = nullptr;
+  afi_ctx *c = new (std::nothrow) afi_ctx();
+  if (!c) { set_error("host allocation failed"); return AFI_ENOMEM; }
+  afi_status st = setup_context(prob, opt, c);
+  if (st != AFI_OK) {
+    free_context(c);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return AFI_OK;
+}
+
+void af_ieti_destroy(afi_ctx *c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  free_context(c);
+  delete c;
+}
+
+afi_status fd_apply(afi_ctx *c, int interior, const double *r, double *s, int nrhs, void *stream) {
+  if (!c || !r || !s || nrhs < 1 || (interior != 0 && interior != 1)) {
+    set_error("fd_apply: invalid argument");
+    return AFI_EINVAL;
+  }
+  const long len = interior ? c->dim * 0 + c->n_int : c->n_dof;
+  for (int j = 0; j < nrhs; ++j)
+    AFI_TRY(fd_run(c, interior, r + (long long)j * len, s + (long long)j * len, as_stream(stream)));
+  return AFI_OK;
+}
+
+static afi_status solve_many(afi_ctx *c, const double *f, double *u, double *lam, int nrhs,
+                             afi_info *info, void *stream) {
+  if (!c || !f || !u || nrhs < 1) { set_error("solve: invalid argument"); return AFI_EINVAL; }
+  afi_status worst = AFI_OK;
+  for (int j = 0; j < nrhs; ++j) {
+    afi_status st = solve_one(c, f + (long long)j * c->n_dof, u + (long long)j * c->n_dof,
+                              lam ? lam + (long long)j * c->n_c : nullptr, info, as_stream(stream));
+    if (st == AFI_EBREAKDOWN || st == AFI_ECUDA || st == AFI_EINVAL || st == AFI_ENOMEM) return st;
+    if (st != AFI_OK) worst = st;
+  }
+  return worst;
+}
+
+afi_status ieti_solve(afi_ctx *c, const double *f, double *u, double *lam, int nrhs,
+                      afi_info *info, void *stream) {
+  return solve_many(c, f, u, lam, nrhs, info, stream);
+}
+
+afi_status ieti_solve_adjoint(afi_ctx *c, const double *g, double *z, double *zl, int nrhs,
+                              afi_info *info, void *stream) {
+  return solve_many(c, g, z, zl, nrhs, info, stream);
+}
+
+afi_status afi_lame_grad(afi_ctx *c, const double *u, const double *z, double *grad, void *stream) {
+  if (!c || !u || !z || !grad) { set_error("afi_lame_grad: invalid argument"); return AFI_EINVAL; }
+  return op_lame_grad(c, u, z, grad, as_stream(stream));
+}
+
+afi_status afi_load_vector(afi_ctx *c, const double *coef, double *f, void *stream) {
+  if (!c || !coef || !f) { set_error("afi_load_vector: invalid argument"); return AFI_EINVAL; }
+  return op_load(c, coef, f, as_stream(stream));
+}
+
+afi_status afi_apply(afi_ctx *c, afi_operator op, const double *x, double *y, void *stream) {
+  if (!c || !x || !y) { set_error("afi_apply: invalid argument"); return AFI_EINVAL; }
+  cudaStream_t s = as_stream(stream);
+  switch (op) {
+    case AFI_OP_STIFFNESS: return op_stiffness(c, x, y, s);
+    case AFI_OP_B: return op_B(c, x, y, s);
+    case AFI_OP_BT: return op_Bt(c, x, y, false, true, s);
+    case AFI_OP_PCHI: return op_Pchi(c, x, y, s);
+    case AFI_OP_PU: return op_Pu(c, x, y, s);
+    case AFI_OP_PA_INV: return fd_run(c, 0, x, y, s);
+    case AFI_OP_SCHUR: return schur_run(c, x, y, s);
+    case AFI_OP_PS: return op_PS(c, x, y, s);
+    case AFI_OP_PRECOND: return op_precond(c, x, y, s);
+    case AFI_OP_SADDLE: return op_saddle(c, x, y, s);
+    default: set_error("afi_apply: unknown operator"); return AFI_EINVAL;
+  }
+}
+
+afi_status afi_set_precision(afi_ctx *c, afi_fd_precision prec) {
+  if (!c || prec < AFI_FD_FP64 || prec > AFI_FD_BF16) { set_error("afi_set_precision: invalid"); return AFI_EINVAL; }
+  c->opt.prec = prec;
+  return AFI_OK;
+}
+
+afi_status afi_sizes(const afi_ctx *c, long *n_dof, long *n_c) {
+  if (!c) { set_error("afi_sizes: null context"); return AFI_EINVAL; }
+  if (n_dof) *n_dof = c->n_dof;
+  if (n_c) *n_c = c->n_c;
+  return AFI_OK;
+}
+
+afi_status afi_memory(const afi_ctx *c, long long *total, long long *stiff) {
+  if (!c) { set_error("afi_memory: null context"); return AFI_EINVAL; }
+  if (total) *total = c->bytes;
+  if (stiff) *stiff = c->stencil_n * (long long)sizeof(double);
+  return AFI_OK;
+}
+
+const char *afi_status_string(afi_status s) {
+  switch (s) {
+    case AFI_OK: return "ok";
+    case AFI_EINVAL: return "invalid argument";
+    case AFI_ENOMEM: return "out of device memory";
+    case AFI_ECUDA: return "CUDA error";
+    case AFI_ESINGULAR: return "singular or indefinite matrix";
+    case AFI_ENOT_CONVERGED: return "not converged";
+    case AFI_EBREAKDOWN: return "MINRES breakdown";
+    case AFI_ETIMEOUT: return "timeout";
+    default: return "unknown status";
+  }
+}
+
+const char *afi_last_error(void) { return last_error_cstr(); }
+
+}  // extern "C"

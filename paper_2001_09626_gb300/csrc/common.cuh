@@ -1,0 +1,170 @@
+// Internal definitions of the AF-IETI library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/afieti.h"
+
+namespace afi {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+
+#define AFI_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      ::afi::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));   \
+      return AFI_ECUDA;                                                       \
+    }                                                                         \
+  } while (0)
+
+#define AFI_TRY(expr)                                                         \
+  do {                                                                        \
+    afi_status s_ = (expr);                                                   \
+    if (s_ != AFI_OK) return s_;                                              \
+  } while (0)
+
+#define AFI_LAUNCH_CHECK() AFI_CUDA(cudaGetLastError())
+
+// ------------------------------------------------------- 1D spline tables
+// One table per distinct (nel, p) pair (open uniform knots).  Offsets index
+// the context's FP64 pool (and FP32 / BF16 pools for the low-precision
+// copies of the eigenvectors).  A "dummy" table (n = 1) stands for the third
+// direction of 2D problems: basis value 1, K = 0, M = 1, U = 1, D = 0.
+struct Tab1D {
+  int nel, p, n, nq, ni;       // ni = interior count (n - 2, or 1 for dummy)
+  long long knots;             // [nel + 2p + 1]
+  long long qw;                // [nq] Gauss weights (times span length)
+  long long val, der;          // [nq][p+1] active basis values / derivatives
+  long long K, M;              // [n][n] univariate stiffness and mass
+  long long U, D;              // [n][n] (row i = basis, col a = mode), [n]
+  long long Ui, Di;            // interior pencil [ni][ni], [ni]
+  long long Uf, Uif;           // FP32 copies (float pool)
+  long long Ub, Uib;           // BF16 copies (bf16 pool), row-major like U
+};
+
+// Per-patch descriptor (device-side POD).
+struct DevPatch {
+  int n[3];         // basis functions per direction (n3 = 1 in 2D)
+  int ni[3];        // interior counts (n - 2; 1 for a dummy direction)
+  int nq[3];        // quadrature points per direction (1 for dummy)
+  int W[3];         // stencil widths 2p+1 (1 for dummy)
+  int tab[3];       // 1D table per direction
+  int p, N, Ni, S;  // degree, nodes, interior nodes, stencil offsets
+  int NQ;           // quadrature points of the patch
+  int pad_;
+  long long off;    // torn offset of component 0
+  long long ioff;   // compact interior offset of component 0
+  long long soff;   // stiffness stencil offset (doubles)
+  long long qoff;   // quadrature geometry offset (points)
+  long long xoff;   // control point offset (doubles)
+  double lam, mu, Hs;  // Lame values, H^{d-2}
+};
+
+struct afi_ctx_impl;
+
+}  // namespace afi
+
+// The opaque context.
+struct afi_ctx {
+  int dim = 0, npatch = 0, nm = 0;   // nm = rigid modes per patch
+  int device = 0;
+  long n_dof = 0, n_c = 0, n_int = 0;
+  afi_options opt{};
+  double t_setup_ms = 0.0;
+
+  // host copies
+  std::vector<afi::DevPatch> hp;
+  std::vector<afi::Tab1D> htab;
+  int max_N = 0, max_n = 0;
+
+  // device data
+  afi::DevPatch *patches = nullptr;
+  afi::Tab1D *tabs = nullptr;
+  double *dpool = nullptr;  long long dpool_n = 0;
+  float *fpool = nullptr;   long long fpool_n = 0;
+  __nv_bfloat16 *bpool = nullptr; long long bpool_n = 0;
+  double *ctrl = nullptr;                     // all control points
+  double *stencil = nullptr; long long stencil_n = 0;
+  double *qgeo = nullptr; long long nqp = 0;  // [DIM*DIM + 1][nqp] SoA
+
+  // constraints
+  int2 *row_copy = nullptr;      // (dofA, dofB or -1) per row
+  int2 *row_grp = nullptr;       // (group start, copies m; m = 0 -> Dirichlet)
+  int2 *row_patch = nullptr;     // (patch of copy A, patch of copy B or -1)
+  int *shell_dof = nullptr;      // torn index of each shell copy-dof
+  int *bt_ptr = nullptr;         // CSR over shell dofs
+  int *bt_ent = nullptr;         // row*2 + (sign < 0)
+  long n_shell = 0;
+  int *prow_ptr = nullptr;       // per patch: rows touching the patch
+  int2 *prow_ent = nullptr;      // (row*2 + neg, dof)
+  int *pair_ptr = nullptr;       // G^T G off-diagonal pair blocks
+  int2 *pair_kk = nullptr;       // (k, k')
+  int4 *pair_ent = nullptr;      // (dofA, dofB, sign product, unused)
+  int npairs = 0;
+  double *GtG = nullptr;         // [ng][ng] then overwritten by the inverse
+  double *GtG_inv = nullptr;
+  double *RtR_inv = nullptr;     // [npatch][nm][nm]
+  int ng = 0;
+
+  // workspaces
+  double *ws = nullptr; long long ws_n = 0;     // general FP64 workspace
+  double *fdscratch = nullptr; long long fdscratch_n = 0;
+  double *small = nullptr;                      // reduction / scalar area
+  double *host_small = nullptr;                 // pinned host mirror
+  int *dflag = nullptr;
+
+  long long bytes = 0;
+};
+
+namespace afi {
+
+constexpr int kSmallDoubles = 1 << 16;   // reduction scratch (partials + scalars)
+constexpr int kOpScratch = 5;            // operator scratch, in units of (n_dof + n_c)
+constexpr int kKrylov = 11;              // MINRES vectors of length n_dof + n_c
+
+// allocation helper that records bytes
+afi_status dalloc(afi_ctx *c, void **p, size_t bytes);
+
+// ----------------------------------------------------------- kernels API
+// setup.cu
+afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ctx *c);
+void free_context(afi_ctx *c);
+
+// ops.cu (FP64 operators on the hot path)
+afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_B(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_Bt(afi_ctx *c, const double *x, double *y, bool accumulate, bool zero_first,
+                 cudaStream_t s);
+afi_status op_Pchi(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_Pu(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_BBt_inv(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_Gt_rows(afi_ctx *c, const double *x, double *g, cudaStream_t s);
+afi_status op_Rt(afi_ctx *c, const double *x, double *g, cudaStream_t s);
+afi_status op_dense_inv(afi_ctx *c, const double *g, double *y, cudaStream_t s);
+afi_status op_G(afi_ctx *c, const double *y, double *out, bool subtract, cudaStream_t s);
+afi_status op_R_sub(afi_ctx *c, const double *y, double *v, cudaStream_t s);
+afi_status op_PS(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_precond(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_saddle(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_load(afi_ctx *c, const double *coef, double *f, cudaStream_t s);
+afi_status op_lame_grad(afi_ctx *c, const double *u, const double *z, double *g,
+                        cudaStream_t s);
+afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam, afi_info *info,
+                     cudaStream_t s);
+
+// fd.cu (local solvers: Algorithm 1 and the parametric Schur complement)
+afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st);
+afi_status schur_run(afi_ctx *c, const double *t, double *y, cudaStream_t st);
+afi_status fd_prepare(afi_ctx *c);
+
+// reductions (ops.cu)
+afi_status dot(afi_ctx *c, const double *a, const double *b, long n, double *dst,
+               cudaStream_t s);
+
+}  // namespace afi

@@ -1,4 +1,4 @@
-"""Pins for the oracle's Fast Diagonalization (Algorithm 1, eqs. 5.6-5.8):
+"""Pins for the oracle's Fast Diagonalization (Algorithm 1, eqs. 5.8-5.10):
 the generalised eigen identities, the FD solve against a dense direct solve of
 the Kronecker-sum system on small patches (3D and 2D, every component),
 invariance to eigenvector signs and the interior variant."""
@@ -49,7 +49,7 @@ def test_fd_equals_dense_kronecker_solve(nels, p, H):
         # FD(P r) = r
         back = fd.fd_solve((P @ r).reshape(ns[::-1]), U, lam).reshape(-1)
         np.testing.assert_allclose(back, r, atol=1e-9)
-        # Lambda is the diagonalised operator, eq. 5.7
+        # Lambda is the diagonalised operator, eq. 5.9
         Uk = fd.kron_list(U)
         np.testing.assert_allclose(Uk.T @ P @ Uk, np.diag(lam.reshape(-1)),
                                    atol=1e-9 * lam.max())

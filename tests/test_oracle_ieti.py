@@ -2,7 +2,7 @@
 constraint count against dim of the conforming space, full row rank and the
 block-diagonal B B^T, the projector identities, lambda_0, the iterative
 solution against the conforming direct solve (the unique solution of
-eq. 4.2), vanishing jumps, the monotone MINRES estimate and MINRES against a
+eq. 4.5), vanishing jumps, the monotone MINRES estimate and MINRES against a
 dense solve; plus the adjoint gradients against central finite differences."""
 import numpy as np
 import pytest
