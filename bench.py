@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 AF-IETI solver on the C2 workload.
+
+Workload (C2): 3D compressible elasticity (E = 1, nu = 0.3) on the unit cube
+split into 4x4x4 patches, degree 3, C^2 splines on 16^3 elements per patch,
+interior control points jittered by up to 10% of the element size (seeded),
+all-floating with Dirichlet conditions on the whole outer boundary, body
+force with uniform[-1,1] nodal coefficients (seeded), preconditioned MINRES
+to 1e-8 relative residual (estimate and true FP64 residual).
+
+One step = one complete AF-IETI solve (lambda_0, MINRES, recovery) with the
+load vector resident in HBM.  The per-step inputs are larger than L2: every
+iteration streams the 10.8 GB FP64 stiffness stencil.
+
+  python bench.py [--gpus N --steps K --warmup W --prec fp32|fp64|tf32|bf16]
+  python bench.py --impl reference ...   (the CPU oracle as the reference arm)
+
+With N > 1 (torchrun) every rank solves its own seeded right-hand side on its
+own GPU (replicas, weak scaling); the solve has no cross-GPU exchange.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+_CORES = len(os.sched_getaffinity(0))
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(_CORES))
+
+METRIC = "AF-IETI solve time and FD-apply DoF/s, mixed vs FP64 plain, at 1e-8 residual"
+WORKLOAD = ("C2: unit cube, 4x4x4 patches, p=3, C^2, 16^3 elements/patch, 10% interior jitter, "
+            "E=1 nu=0.3, Dirichlet outer boundary, seeded uniform[-1,1] body-force coefficients, "
+            "MINRES tol 1e-8")
+SAMPLE = "C2-mid"          # oracle sample: same geometry kind, 3x3x3 patches, 6^3 elements
+FP64_PEAK_TFLOPS = 1.20    # FP64 FMA throughput measured on this GB300 (2 FMA/clk/SM)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--workload", default="C2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle arm
+def oracle_sample_time(steps=1, warmup=0):
+    """Time the CPU oracle's AF-IETI solve on the bounded sample and scale it
+    to the C2 workload by the DoF ratio (iteration counts of the method are
+    independent of h and H, Theorem 1; the oracle's per-iteration work is
+    linear in the DoF count).  Returns (seconds for C2, details)."""
+    import numpy as np  # noqa: F401
+    import afi_workloads as W
+    from oracle.ieti import AFIETI
+    t = time.time()
+    P = W.config(SAMPLE)
+    s = AFIETI(P)
+    s.assemble()
+    s._local()
+    f = s.load(W.body_force_coeffs(P))
+    prep = time.time() - t
+    n_c2 = W.config("C2").ndof
+    times, iters = [], 0
+    for i in range(warmup + steps):
+        t0 = time.time()
+        _, _, info = s.solve(f, tol=1e-8)
+        if i >= warmup:
+            times.append(time.time() - t0)
+        iters = info["iters"]
+    per = sum(times) / len(times)
+    scale = n_c2 / s.ndof
+    return per * scale, {"sample": f"{SAMPLE} (3x3x3 jittered cube patches, p=3, 6^3 elements, "
+                                   f"{s.ndof} DoF) full oracle AF-IETI solve to 1e-8, "
+                                   f"{iters} iterations, {per:.2f} s; scaled x{scale:.1f} by DoF "
+                                   f"to C2 (projection)", "prep_s": round(prep, 1),
+                         "sample_s": round(per, 3), "cores": _CORES}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    val, det = oracle_sample_time(steps=args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(val * 1e3, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": round(val, 3), "unit": "s", "cores": det["cores"],
+                             "kind": "oracle", "sample": det["sample"]},
+            "e2e": {"value": round(val, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- our arm
+def stencil_stats(prob):
+    """Algorithmic FLOPs and stored bytes of one stiffness matvec."""
+    d = prob.dim
+    nnz, stored, ndof = 0, 0, 0
+    for k in range(prob.npatch):
+        p = int(prob.degree[k])
+        ns = prob.n(k)
+        rows = 1
+        for n in ns:
+            rows *= n * (2 * p + 1) - p * (p + 1)
+        nnz += d * d * rows
+        N = 1
+        for n in ns:
+            N *= n
+        stored += d * d * (2 * p + 1) ** d * N
+        ndof += d * N
+    return 2 * nnz, stored * 8 + 2 * ndof * 8
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current source of that kernel."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        parts = ln.split()
+        if len(parts) >= 3 and parts[0] == kernel:
+            src = os.path.join(ROOT, "paper_2001_09626_gb300", "csrc", parts[2])
+            if len(parts) >= 4 and os.path.exists(src):
+                h = hashlib.md5(open(src, "rb").read()).hexdigest()[:12]
+                if h != parts[3]:
+                    return None
+            return float(parts[1])
+    return None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    import afi_workloads as W
+    from paper_2001_09626_gb300 import afieti as A
+    from paper_2001_09626_gb300.solver import Solver
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    prob = W.config(args.workload)
+    coeffs = W.body_force_coeffs(prob, seed=rank)
+    t0 = time.time()
+    s = Solver(prob, prec=args.prec, tol=1e-8, maxit=5000)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    f = s.load_vector(coeffs)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for _ in range(args.warmup):
+        s.solve(f)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    L0 = A.afi_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        u, lam = s.solve(f)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = (A.afi_kernel_launches() - L0) // args.steps
+    clocks = sampler.stop()
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps)
+    info = dict(s.last_info)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    f_h = f.cpu().pin_memory()
+    u_h = torch.empty_like(f_h).pin_memory()
+    f_d = torch.empty_like(f)
+    u_d = torch.empty_like(f)
+    lam_d = s.zeros(s.n_c)
+
+    def e2e_step():
+        f_d.copy_(f_h, non_blocking=True)
+        A.ieti_solve(s.ctx, f_d, u_d, lam_d, 1)
+        u_h.copy_(u_d, non_blocking=True)
+    e2e_step()
+    barrier()
+    ms_e2e = reduce_max(timed(e2e_step, args.steps))
+
+    # plain FP64 form on the same context, same right-hand side
+    s.set_precision("fp64")
+    s.solve(f)
+    ms_plain = timed(lambda: s.solve(f), max(1, min(args.steps, 3)))
+    info_plain = dict(s.last_info)
+
+    # FD apply throughput (P_A^{-1} on every patch and component)
+    r = torch.rand(s.n_dof, dtype=torch.float64, device="cuda")
+    fd_ms = {}
+    for prec in ("fp64", args.prec):
+        s.set_precision(prec)
+        for _ in range(3):
+            s.fd(r)
+        fd_ms[prec] = timed(lambda: s.fd(r), 20)
+    s.set_precision(args.prec)
+
+    # dominant kernel: FP64 stiffness matvec (one launch per apply)
+    x = torch.rand(s.n_dof, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        s.apply(A.AFI_OP_STIFFNESS, x)
+    mv_ms = timed(lambda: s.apply(A.AFI_OP_STIFFNESS, x), 20)
+    flops, stored_bytes = stencil_stats(prob)
+    achieved = flops / (mv_ms * 1e-3) / 1e12
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 3),
+                "traffic": traffic_record("k_stencil_mv"),
+                "kernel": "k_stencil_mv<3> (FP64 stiffness stencil matvec)",
+                "flops_per_launch": flops, "launch_ms": round(mv_ms, 4),
+                "peak_source": "FP64 FMA probe on GB300 (measured, not in MEASURED_PEAKS.json)",
+                "hbm_view": {"bytes_per_launch": stored_bytes,
+                             "GBs": round(stored_bytes / (mv_ms * 1e-3) / 1e9, 1),
+                             "peak_GBs": hbm, "frac": round(stored_bytes / (mv_ms * 1e-3) / 1e9 / hbm, 3)}}
+    fd_bytes = 16 * s.n_dof
+    roofline_fd = {"bound": "hbm", "kernel": f"k_fd ({args.prec} local solver)",
+                   "achieved": round(fd_bytes / (fd_ms[args.prec] * 1e-3) / 1e9, 1),
+                   "peak": hbm, "unit": "GB/s",
+                   "frac": round(fd_bytes / (fd_ms[args.prec] * 1e-3) / 1e9 / hbm, 4),
+                   "traffic": traffic_record("k_fd"), "bytes_per_launch": fd_bytes}
+
+    line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_dof": s.n_dof, "n_c": s.n_c,
+                       "local_solver_precision": args.prec,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (10.8 GB stencil streamed each iteration)"},
+            "iterations": info["iters"], "relres_true": info["relres_true"],
+            "setup_s": round(setup_s, 3),
+            "plain_fp64": {"solve_s": round(ms_plain / 1e3, 4), "iterations": info_plain["iters"],
+                           "relres_true": info_plain["relres_true"]},
+            "fd_apply_dofs_per_s": {k: round(s.n_dof / (v * 1e-3), 1) for k, v in fd_ms.items()},
+            "e2e": {"value": round(ms_e2e / 1e3, 4), "unit": "s",
+                    "h2d_bytes_per_step": 8 * s.n_dof, "d2h_bytes_per_step": 8 * s.n_dof},
+            "gpu_launches": int(launches), "roofline": roofline, "roofline_fd": roofline_fd,
+            "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        val, det = oracle_sample_time(steps=1, warmup=0)
+        line["cpu_baseline"] = {"value": round(val, 3), "unit": "s", "cores": det["cores"],
+                                "kind": "oracle", "sample": det["sample"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -184,7 +184,14 @@ afi_status afi_memory(const afi_ctx *ctx, long long *total_bytes, long long *sti
 
 void af_ieti_destroy(afi_ctx *ctx);
 const char *afi_status_string(afi_status s);
+
+/* Message of the most recent failure in this process (not thread-specific). */
 const char *afi_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all contexts, all threads); the difference of two readings counts the
+ * launches in between. */
+long long afi_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -66,9 +66,9 @@ class PatchGeometry:
         W = [self.qw[j][qr[j][0]:qr[j][1]] for j in range(d)]
 
         def kron(tabs):
-            out = np.array([[1.0]])
+            out = sp.csr_matrix(np.array([[1.0]]))
             for t in tabs:
-                out = np.kron(t, out)
+                out = sp.kron(sp.csr_matrix(t), out, format="csr")
             return out
         Phi0 = kron(T0)
         Phis = [kron([T1[j] if j == a else T0[j] for j in range(d)]) for a in range(d)]
@@ -89,7 +89,7 @@ class PatchGeometry:
         """J[q, x, a] = d F_x / d eta_a at the quadrature points (isoparametric
         spline map F = sum_i P_i B_i, Section 2.2)."""
         Xc = self.X[cols]
-        return np.stack([Ph @ Xc for Ph in Phis], axis=-1)
+        return np.stack([np.asarray(Ph @ Xc) for Ph in Phis], axis=-1)
 
 
 def _geometry_block(g: PatchGeometry, qr, cr):
@@ -123,13 +123,22 @@ def stiffness_block(g: PatchGeometry, lam: float, mu: float, qr=None, cr=None):
         raise ValueError("singular geometry map")
     wd = w * np.abs(det)
     # physical gradients G[x][q, i] = sum_a Q[q, a, x] Phi_a[q, i]
-    G = [sum(Q[:, a, x][:, None] * Phis[a] for a in range(d)) for x in range(d)]
+    G = [sum(sp.diags(Q[:, a, x]) @ Phis[a] for a in range(d)).tocsr() for x in range(d)]
+    Wd = sp.diags(wd)
+    # P[x][y] = int d_x B_i d_y B_j  (quadrature), P[y][x] = P[x][y]^T
+    P = [[None] * d for _ in range(d)]
+    for x in range(d):
+        WGx = (Wd @ G[x]).tocsc()
+        for y in range(x, d):
+            P[y][x] = (G[y].T @ WGx).toarray()
+            if y != x:
+                P[x][y] = P[y][x].T
     nc = len(cols)
     A = np.zeros((d * nc, d * nc))
-    grad = sum(G[x].T @ (wd[:, None] * G[x]) for x in range(d))
+    grad = sum(P[x][x] for x in range(d))
     for l in range(d):
         for m in range(d):
-            blk = mu * (G[m].T @ (wd[:, None] * G[l])) + lam * (G[l].T @ (wd[:, None] * G[m]))
+            blk = mu * P[m][l] + lam * P[l][m]
             if l == m:
                 blk = blk + mu * grad
             A[l * nc:(l + 1) * nc, m * nc:(m + 1) * nc] = blk
@@ -149,7 +158,7 @@ def mass_block(g: PatchGeometry, qr=None, cr=None):
     cr = g.full_c() if cr is None else cr
     Phi0, Phis, w, cols, det, Q = _geometry_block(g, qr, cr)
     wd = w * np.abs(det)
-    return Phi0.T @ (wd[:, None] * Phi0), cols
+    return (Phi0.T @ sp.diags(wd) @ Phi0).toarray(), cols
 
 
 def stiffness(g: PatchGeometry, lam: float, mu: float) -> np.ndarray:
@@ -168,7 +177,7 @@ def load_from_function(g: PatchGeometry, fun) -> np.ndarray:
     qr, cr = g.full_q(), g.full_c()
     Phi0, Phis, w, cols, det, Q = _geometry_block(g, qr, cr)
     wd = w * np.abs(det)
-    xq = Phi0 @ g.X[cols]
+    xq = np.asarray(Phi0 @ g.X[cols])
     fv = fun(xq)
     return np.concatenate([Phi0.T @ (wd * fv[:, l]) for l in range(g.dim)])
 

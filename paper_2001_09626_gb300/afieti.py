@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": AFI_FD_FP64, "fp32": AFI_FD_FP32, "tf32": AFI_FD_TF32, "bf
 
 EXPORTED = ["af_ieti_setup", "fd_apply", "ieti_solve", "ieti_solve_adjoint", "afi_lame_grad",
             "afi_load_vector", "afi_apply", "afi_set_precision", "afi_sizes", "afi_memory",
-            "af_ieti_destroy", "afi_status_string", "afi_last_error"]
+            "af_ieti_destroy", "afi_status_string", "afi_last_error", "afi_kernel_launches"]
 
 
 class afi_problem(C.Structure):
@@ -85,8 +85,11 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.afi_status_string.restype = C.c_char_p
     lib.afi_last_error.argtypes = []
     lib.afi_last_error.restype = C.c_char_p
+    lib.afi_kernel_launches.argtypes = []
+    lib.afi_kernel_launches.restype = C.c_longlong
     for name in EXPORTED:
-        if name not in ("af_ieti_destroy", "afi_status_string", "afi_last_error"):
+        if name not in ("af_ieti_destroy", "afi_status_string", "afi_last_error",
+                        "afi_kernel_launches"):
             getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -98,6 +101,10 @@ def afi_status_string(status: int) -> str:
 
 def afi_last_error() -> str:
     return load().afi_last_error().decode()
+
+
+def afi_kernel_launches() -> int:
+    return int(load().afi_kernel_launches())
 
 
 def _check(status, where, allow=()):

@@ -38,7 +38,7 @@ afi_status fd_apply(afi_ctx *c, int interior, const double *r, double *s, int nr
     set_error("fd_apply: invalid argument");
     return AFI_EINVAL;
   }
-  const long len = interior ? c->dim * 0 + c->n_int : c->n_dof;
+  const long len = interior ? c->n_int : c->n_dof;
   for (int j = 0; j < nrhs; ++j)
     AFI_TRY(fd_run(c, interior, r + (long long)j * len, s + (long long)j * len, as_stream(stream)));
   return AFI_OK;
@@ -130,5 +130,7 @@ const char *afi_status_string(afi_status s) {
 }
 
 const char *afi_last_error(void) { return last_error_cstr(); }
+
+long long afi_kernel_launches(void) { return g_launches.load(); }
 
 }  // extern "C"

@@ -318,14 +318,14 @@ afi_status assemble_stiffness(afi_ctx *c) {
     for (int a = 0; a < D && st == AFI_OK; ++a)
       for (int b = 0; b < D; ++b) {
         if (D == 3) {
-          k_asm1<3><<<dim3(maxline, nb), 128, smem1>>>(c->patches, dbatch, c->tabs, c->dpool,
+          launch(k_asm1<3>, dim3(maxline, nb), 128, smem1, 0, c->patches, dbatch, c->tabs, c->dpool,
                                                        c->qgeo, c->nqp, scratch, doff, a, b);
-          k_asm2<3><<<dim3(maxq3, nb), 128>>>(c->patches, dbatch, c->tabs, c->dpool, scratch,
+          launch(k_asm2<3>, dim3(maxq3, nb), 128, 0, 0, c->patches, dbatch, c->tabs, c->dpool, scratch,
                                               doff, scratch, doff + nb, a, b);
         } else {
-          k_asm1<2><<<dim3(maxline, nb), 128, smem1>>>(c->patches, dbatch, c->tabs, c->dpool,
+          launch(k_asm1<2>, dim3(maxline, nb), 128, smem1, 0, c->patches, dbatch, c->tabs, c->dpool,
                                                        c->qgeo, c->nqp, scratch, doff, a, b);
-          k_asm2<2><<<dim3(maxq3, nb), 128>>>(c->patches, dbatch, c->tabs, c->dpool, scratch,
+          launch(k_asm2<2>, dim3(maxq3, nb), 128, 0, 0, c->patches, dbatch, c->tabs, c->dpool, scratch,
                                               doff, scratch, doff + nb, a, b);
         }
         if (cudaGetLastError() != cudaSuccess) { st = AFI_ECUDA; break; }
@@ -333,10 +333,10 @@ afi_status assemble_stiffness(afi_ctx *c) {
     if (st != AFI_OK) break;
     unsigned g3 = (unsigned)((maxcols + 127) / 128);
     if (D == 3)
-      k_asm3<3><<<dim3(g3, nb), 128>>>(c->patches, dbatch, c->tabs, c->dpool, scratch, doff + nb,
+      launch(k_asm3<3>, dim3(g3, nb), 128, 0, 0, c->patches, dbatch, c->tabs, c->dpool, scratch, doff + nb,
                                        c->stencil);
     else
-      k_asm3<2><<<dim3(g3, nb), 128>>>(c->patches, dbatch, c->tabs, c->dpool, scratch, doff + nb,
+      launch(k_asm3<2>, dim3(g3, nb), 128, 0, 0, c->patches, dbatch, c->tabs, c->dpool, scratch, doff + nb,
                                        c->stencil);
     if (cudaGetLastError() != cudaSuccess) st = AFI_ECUDA;
     k0 += nb;
@@ -345,8 +345,8 @@ afi_status assemble_stiffness(afi_ctx *c) {
     long long maxSN = 1;
     for (auto &p : c->hp) maxSN = std::max(maxSN, (long long)p.S * p.N);
     dim3 g((unsigned)((maxSN + 255) / 256), c->npatch);
-    if (D == 3) k_asm_fill<3><<<g, 256>>>(c->patches, c->stencil);
-    else k_asm_fill<2><<<g, 256>>>(c->patches, c->stencil);
+    if (D == 3) launch(k_asm_fill<3>, g, 256, 0, 0, c->patches, c->stencil);
+    else launch(k_asm_fill<2>, g, 256, 0, 0, c->patches, c->stencil);
     if (cudaGetLastError() != cudaSuccess) st = AFI_ECUDA;
   }
   cudaError_t e = cudaDeviceSynchronize();
@@ -363,8 +363,8 @@ afi_status compute_geometry(afi_ctx *c) {
   for (auto &p : c->hp) maxNQ = std::max(maxNQ, p.NQ);
   dim3 g((maxNQ + 127) / 128, c->npatch);
   AFI_CUDA(cudaMemset(c->dflag, 0, sizeof(int)));
-  if (c->dim == 3) k_geometry<3><<<g, 128>>>(c->patches, c->tabs, c->dpool, c->ctrl, c->qgeo, c->nqp, c->dflag);
-  else k_geometry<2><<<g, 128>>>(c->patches, c->tabs, c->dpool, c->ctrl, c->qgeo, c->nqp, c->dflag);
+  if (c->dim == 3) launch(k_geometry<3>, g, 128, 0, 0, c->patches, c->tabs, c->dpool, c->ctrl, c->qgeo, c->nqp, c->dflag);
+  else launch(k_geometry<2>, g, 128, 0, 0, c->patches, c->tabs, c->dpool, c->ctrl, c->qgeo, c->nqp, c->dflag);
   AFI_LAUNCH_CHECK();
   int h = 0;
   AFI_CUDA(cudaMemcpy(&h, c->dflag, sizeof(int), cudaMemcpyDeviceToHost));
@@ -517,11 +517,11 @@ afi_status op_load(afi_ctx *c, const double *coef, double *f, cudaStream_t s) {
   AFI_CUDA(cudaMallocAsync((void **)&cq, (size_t)D * c->nqp * sizeof(double), s));
   dim3 g((maxNQ + 127) / 128, c->npatch), g2((maxN + 127) / 128, c->npatch);
   if (D == 3) {
-    k_eval_qp<3><<<g, 128, 0, s>>>(c->patches, c->tabs, c->dpool, coef, cq, c->nqp, 0);
-    k_mass_gather<3><<<g2, 128, 0, s>>>(c->patches, c->tabs, c->dpool, c->qgeo, cq, f, c->nqp);
+    launch(k_eval_qp<3>, g, 128, 0, s, c->patches, c->tabs, c->dpool, coef, cq, c->nqp, 0);
+    launch(k_mass_gather<3>, g2, 128, 0, s, c->patches, c->tabs, c->dpool, c->qgeo, cq, f, c->nqp);
   } else {
-    k_eval_qp<2><<<g, 128, 0, s>>>(c->patches, c->tabs, c->dpool, coef, cq, c->nqp, 0);
-    k_mass_gather<2><<<g2, 128, 0, s>>>(c->patches, c->tabs, c->dpool, c->qgeo, cq, f, c->nqp);
+    launch(k_eval_qp<2>, g, 128, 0, s, c->patches, c->tabs, c->dpool, coef, cq, c->nqp, 0);
+    launch(k_mass_gather<2>, g2, 128, 0, s, c->patches, c->tabs, c->dpool, c->qgeo, cq, f, c->nqp);
   }
   AFI_LAUNCH_CHECK();
   AFI_CUDA(cudaFreeAsync(cq, s));
@@ -539,15 +539,15 @@ afi_status op_lame_grad(afi_ctx *c, const double *u, const double *z, double *gr
   double *gz = gu + (long long)D * D * c->nqp, *part = gz + (long long)D * D * c->nqp;
   dim3 g((maxNQ + 127) / 128, c->npatch);
   if (D == 3) {
-    k_eval_qp<3><<<g, 128, 0, s>>>(c->patches, c->tabs, c->dpool, u, gu, c->nqp, 1);
-    k_eval_qp<3><<<g, 128, 0, s>>>(c->patches, c->tabs, c->dpool, z, gz, c->nqp, 1);
-    k_lame_density<3><<<dim3(nblk, c->npatch), 256, 0, s>>>(c->patches, c->qgeo, gu, gz, c->nqp, part, nblk);
+    launch(k_eval_qp<3>, g, 128, 0, s, c->patches, c->tabs, c->dpool, u, gu, c->nqp, 1);
+    launch(k_eval_qp<3>, g, 128, 0, s, c->patches, c->tabs, c->dpool, z, gz, c->nqp, 1);
+    launch(k_lame_density<3>, dim3(nblk, c->npatch), 256, 0, s, c->patches, c->qgeo, gu, gz, c->nqp, part, nblk);
   } else {
-    k_eval_qp<2><<<g, 128, 0, s>>>(c->patches, c->tabs, c->dpool, u, gu, c->nqp, 1);
-    k_eval_qp<2><<<g, 128, 0, s>>>(c->patches, c->tabs, c->dpool, z, gz, c->nqp, 1);
-    k_lame_density<2><<<dim3(nblk, c->npatch), 256, 0, s>>>(c->patches, c->qgeo, gu, gz, c->nqp, part, nblk);
+    launch(k_eval_qp<2>, g, 128, 0, s, c->patches, c->tabs, c->dpool, u, gu, c->nqp, 1);
+    launch(k_eval_qp<2>, g, 128, 0, s, c->patches, c->tabs, c->dpool, z, gz, c->nqp, 1);
+    launch(k_lame_density<2>, dim3(nblk, c->npatch), 256, 0, s, c->patches, c->qgeo, gu, gz, c->nqp, part, nblk);
   }
-  k_lame_final<<<(c->npatch + 127) / 128, 128, 0, s>>>(part, nblk, c->npatch, grad);
+  launch(k_lame_final, (c->npatch + 127) / 128, 128, 0, s, part, nblk, c->npatch, grad);
   AFI_LAUNCH_CHECK();
   AFI_CUDA(cudaFreeAsync(gu, s));
   return AFI_OK;

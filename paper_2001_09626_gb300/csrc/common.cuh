@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -30,6 +31,17 @@ void set_error(const std::string &msg);
   } while (0)
 
 #define AFI_LAUNCH_CHECK() AFI_CUDA(cudaGetLastError())
+
+// Every kernel launch of the library goes through launch(), which counts it
+// (afi_kernel_launches) before the ordinary <<<>>> launch.
+extern std::atomic<long long> g_launches;
+
+template <typename Kernel, typename... Args>
+inline void launch(Kernel kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                   Args... args) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  kernel<<<grid, block, smem, stream>>>(args...);
+}
 
 // ------------------------------------------------------- 1D spline tables
 // One table per distinct (nel, p) pair (open uniform knots).  Offsets index

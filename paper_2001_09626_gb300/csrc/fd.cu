@@ -247,7 +247,7 @@ static afi_status fd_launch(afi_ctx *c, int interior, const double *r, double *s
   int use_smem = smem <= (size_t)smem_limit();
   if (use_smem) AFI_CUDA(cudaFuncSetAttribute(k_fd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   else smem = 0;
-  k_fd<T><<<dim3(c->npatch, c->dim), 256, smem, st>>>(c->patches, c->tabs, c->dpool, Pool<T>::get(c),
+  launch(k_fd<T>, dim3(c->npatch, c->dim), 256, smem, st, c->patches, c->tabs, c->dpool, Pool<T>::get(c),
                                                      c->dim, interior, r, s,
                                                      reinterpret_cast<T *>(c->fdscratch), use_smem);
   AFI_LAUNCH_CHECK();
@@ -260,7 +260,7 @@ static afi_status schur_launch(afi_ctx *c, const double *t, double *y, cudaStrea
   int use_smem = smem <= (size_t)smem_limit();
   if (use_smem) AFI_CUDA(cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   else smem = 0;
-  k_schur<T><<<dim3(c->npatch, c->dim), 256, smem, st>>>(c->patches, c->tabs, c->dpool, Pool<T>::get(c),
+  launch(k_schur<T>, dim3(c->npatch, c->dim), 256, smem, st, c->patches, c->tabs, c->dpool, Pool<T>::get(c),
                                                          c->dim, t, y,
                                                          reinterpret_cast<T *>(c->fdscratch), use_smem);
   AFI_LAUNCH_CHECK();

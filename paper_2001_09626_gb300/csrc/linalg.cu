@@ -436,36 +436,36 @@ __global__ void k_small_inv(double *A, int nm, int count, int *flag) {
 // ------------------------------------------------------------ host entry
 afi_status build_1d_tables(afi_ctx *c) {
   const int nt = (int)c->htab.size();
-  k_knots_quad<<<nt, 64>>>(c->tabs, nt, c->dpool);
+  launch(k_knots_quad, nt, 64, 0, 0, c->tabs, nt, c->dpool);
   AFI_LAUNCH_CHECK();
   int maxq = 1, maxn = 1;
   for (auto &t : c->htab) { maxq = std::max(maxq, t.nq); maxn = std::max(maxn, t.n); }
-  k_basis<<<dim3((maxq + 127) / 128, nt), 128>>>(c->tabs, nt, c->dpool);
+  launch(k_basis, dim3((maxq + 127) / 128, nt), 128, 0, 0, c->tabs, nt, c->dpool);
   AFI_LAUNCH_CHECK();
-  k_kmass<<<dim3((maxn * maxn + 127) / 128, nt), 128>>>(c->tabs, nt, c->dpool);
+  launch(k_kmass, dim3((maxn * maxn + 127) / 128, nt), 128, 0, 0, c->tabs, nt, c->dpool);
   AFI_LAUNCH_CHECK();
   size_t smem = 3ull * maxn * maxn * sizeof(double);
   AFI_CUDA(cudaFuncSetAttribute(k_geneig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_geneig<<<nt, 256, smem>>>(c->tabs, nt, c->dpool, 0, c->dflag);
+  launch(k_geneig, nt, 256, smem, 0, c->tabs, nt, c->dpool, 0, c->dflag);
   AFI_LAUNCH_CHECK();
-  k_geneig<<<nt, 256, smem>>>(c->tabs, nt, c->dpool, 1, c->dflag);
+  launch(k_geneig, nt, 256, smem, 0, c->tabs, nt, c->dpool, 1, c->dflag);
   AFI_LAUNCH_CHECK();
   int h = 0;
   AFI_CUDA(cudaMemcpy(&h, c->dflag, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) { set_error("univariate mass pencil not positive definite"); return AFI_ESINGULAR; }
   // low-precision copies of the eigenvectors: the pools mirror the FP64 pool
-  k_to_low<<<(unsigned)((c->dpool_n + 255) / 256), 256>>>(c->dpool, c->fpool, c->bpool, c->dpool_n);
+  launch(k_to_low, (unsigned)((c->dpool_n + 255) / 256), 256, 0, 0, c->dpool, c->fpool, c->bpool, c->dpool_n);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 afi_status dense_spd_inverse(afi_ctx *c, double *A, double *Ainv, int n, double *scratch) {
-  k_chol<<<1, 1024>>>(A, n, c->dflag);
+  launch(k_chol, 1, 1024, 0, 0, A, n, c->dflag);
   AFI_LAUNCH_CHECK();
-  k_trinv<<<(n + 127) / 128, 128>>>(A, scratch, n);
+  launch(k_trinv, (n + 127) / 128, 128, 0, 0, A, scratch, n);
   AFI_LAUNCH_CHECK();
   long long nn = (long long)n * n;
-  k_ltl<<<(unsigned)((nn + 255) / 256), 256>>>(scratch, Ainv, n);
+  launch(k_ltl, (unsigned)((nn + 255) / 256), 256, 0, 0, scratch, Ainv, n);
   AFI_LAUNCH_CHECK();
   int h = 0;
   AFI_CUDA(cudaMemcpy(&h, c->dflag, sizeof(int), cudaMemcpyDeviceToHost));
@@ -474,7 +474,7 @@ afi_status dense_spd_inverse(afi_ctx *c, double *A, double *Ainv, int n, double 
 }
 
 afi_status small_inverses(afi_ctx *c, double *A, int nm, int count) {
-  k_small_inv<<<(count + 63) / 64, 64>>>(A, nm, count, c->dflag);
+  launch(k_small_inv, (count + 63) / 64, 64, 0, 0, A, nm, count, c->dflag);
   AFI_LAUNCH_CHECK();
   int h = 0;
   AFI_CUDA(cudaMemcpy(&h, c->dflag, sizeof(int), cudaMemcpyDeviceToHost));

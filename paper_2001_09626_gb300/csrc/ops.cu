@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(128) k_stencil_mv(const DevPatch *P, const dou
 
 afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   dim3 g((c->max_N + 127) / 128, c->npatch);
-  if (c->dim == 3) k_stencil_mv<3><<<g, 128, 0, s>>>(c->patches, c->stencil, x, y);
-  else k_stencil_mv<2><<<g, 128, 0, s>>>(c->patches, c->stencil, x, y);
+  if (c->dim == 3) launch(k_stencil_mv<3>, g, 128, 0, s, c->patches, c->stencil, x, y);
+  else launch(k_stencil_mv<2>, g, 128, 0, s, c->patches, c->stencil, x, y);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -134,7 +134,7 @@ __global__ void k_BBt_inv(const int2 *grp, long n_c, const double *x, double *y)
 
 afi_status op_B(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->n_c == 0) return AFI_OK;
-  k_B<<<(unsigned)((c->n_c + 255) / 256), 256, 0, s>>>(c->row_copy, c->n_c, x, y, 1.0, 0);
+  launch(k_B, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->row_copy, c->n_c, x, y, 1.0, 0);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -143,7 +143,7 @@ static afi_status op_Bt_scaled(afi_ctx *c, const double *x, double *y, double al
                                bool zero_first, cudaStream_t s) {
   if (zero_first) AFI_CUDA(cudaMemsetAsync(y, 0, c->n_dof * sizeof(double), s));
   if (c->n_shell == 0) return AFI_OK;
-  k_Bt<<<(unsigned)((c->n_shell + 255) / 256), 256, 0, s>>>(c->shell_dof, c->bt_ptr, c->bt_ent,
+  launch(k_Bt, (unsigned)((c->n_shell + 255) / 256), 256, 0, s, c->shell_dof, c->bt_ptr, c->bt_ent,
                                                             c->n_shell, x, y, alpha, acc ? 1 : 0);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
@@ -156,7 +156,7 @@ afi_status op_Bt(afi_ctx *c, const double *x, double *y, bool accumulate, bool z
 
 afi_status op_BBt_inv(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->n_c == 0) return AFI_OK;
-  k_BBt_inv<<<(unsigned)((c->n_c + 255) / 256), 256, 0, s>>>(c->row_grp, c->n_c, x, y);
+  launch(k_BBt_inv, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->row_grp, c->n_c, x, y);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -264,21 +264,21 @@ __global__ void k_G(const DevPatch *P, const double *ctrl, const int2 *rc, const
 }
 
 afi_status op_Gt_rows(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
-  if (c->nm == 6) k_Gt<6><<<c->npatch, 256, 0, s>>>(c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, g, c->dim);
-  else k_Gt<3><<<c->npatch, 256, 0, s>>>(c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, g, c->dim);
+  if (c->nm == 6) launch(k_Gt<6>, c->npatch, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, g, c->dim);
+  else launch(k_Gt<3>, c->npatch, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, g, c->dim);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 afi_status op_Rt(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
-  if (c->nm == 6) k_Rt<6><<<c->npatch, 256, 0, s>>>(c->patches, c->ctrl, x, g, c->dim);
-  else k_Rt<3><<<c->npatch, 256, 0, s>>>(c->patches, c->ctrl, x, g, c->dim);
+  if (c->nm == 6) launch(k_Rt<6>, c->npatch, 256, 0, s, c->patches, c->ctrl, x, g, c->dim);
+  else launch(k_Rt<3>, c->npatch, 256, 0, s, c->patches, c->ctrl, x, g, c->dim);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 afi_status op_dense_inv(afi_ctx *c, const double *g, double *y, cudaStream_t s) {
-  k_dense_mv<<<(c->ng * 32 + 255) / 256, 256, 0, s>>>(c->GtG_inv, g, y, c->ng);
+  launch(k_dense_mv, (c->ng * 32 + 255) / 256, 256, 0, s, c->GtG_inv, g, y, c->ng);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -297,7 +297,7 @@ afi_status op_Pchi(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
 }
 
 static afi_status G_apply(afi_ctx *c, const double *y, double *out, const double *src, cudaStream_t s) {
-  k_G<<<(unsigned)((c->n_c + 255) / 256), 256, 0, s>>>(c->patches, c->ctrl, c->row_copy,
+  launch(k_G, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->patches, c->ctrl, c->row_copy,
                                                        c->row_patch, c->n_c, y, out, c->dim,
                                                        c->nm, src ? 1 : 0, src);
   AFI_LAUNCH_CHECK();
@@ -312,14 +312,14 @@ afi_status op_Pu(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   double *g = gbuf(c, 0);
   AFI_TRY(op_Rt(c, x, g, s));
   dim3 gr((unsigned)((c->dim * c->max_N + 255) / 256), c->npatch);
-  k_Rsub<<<gr, 256, 0, s>>>(c->patches, c->ctrl, x, y, g, c->RtR_inv, c->dim, c->nm);
+  launch(k_Rsub, gr, 256, 0, s, c->patches, c->ctrl, x, y, g, c->RtR_inv, c->dim, c->nm);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 afi_status op_R_sub(afi_ctx *c, const double *y, double *v, cudaStream_t s) {
   dim3 gr((unsigned)((c->dim * c->max_N + 255) / 256), c->npatch);
-  k_Rsub<<<gr, 256, 0, s>>>(c->patches, c->ctrl, v, v, y, nullptr, c->dim, c->nm);
+  launch(k_Rsub, gr, 256, 0, s, c->patches, c->ctrl, v, v, y, nullptr, c->dim, c->nm);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -356,8 +356,8 @@ constexpr int kDotBlocks = 1216;   // 8 per SM on 152 SMs
 constexpr int kPart = 1024;        // offset of the partials in c->small
 
 afi_status dot(afi_ctx *c, const double *a, const double *b, long n, double *dst, cudaStream_t s) {
-  k_dot_partial<<<kDotBlocks, 256, 0, s>>>(a, b, n, c->small + kPart);
-  k_sum_final<<<1, 1024, 0, s>>>(c->small + kPart, kDotBlocks, dst);
+  launch(k_dot_partial, kDotBlocks, 256, 0, s, a, b, n, c->small + kPart);
+  launch(k_sum_final, 1, 1024, 0, s, c->small + kPart, kDotBlocks, dst);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -542,7 +542,7 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   AFI_TRY(op_precond(c, r1, y, s));
   AFI_TRY(dot(c, r1, y, nt, st + S_BETA2, s));
   AFI_TRY(dot(c, b, b, nt, st + S_BNORM2, s));
-  k_minres_init<<<1, 1, 0, s>>>(st);
+  launch(k_minres_init, 1, 1, 0, s, st);
   AFI_LAUNCH_CHECK();
   double *hs = c->host_small;
   AFI_CUDA(cudaMemcpyAsync(hs, st, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -558,18 +558,18 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   double *w1 = wb[0], *w2 = wb[1];
   while (!done && itn < c->opt.maxit) {
     ++itn;
-    k_v_from_y<<<nblk(nt), 256, 0, s>>>(y, v, nt, st);
+    launch(k_v_from_y, nblk(nt), 256, 0, s, y, v, nt, st);
     AFI_TRY(op_saddle(c, v, y, s));
-    k_y_upd1<<<kDotBlocks, 256, 0, s>>>(y, r1, v, nt, st, itn == 1, c->small + kPart);
-    k_sum_final<<<1, 1024, 0, s>>>(c->small + kPart, kDotBlocks, st + S_ALFA);
-    k_y_upd2<<<nblk(nt), 256, 0, s>>>(y, r2, nt, st);
+    launch(k_y_upd1, kDotBlocks, 256, 0, s, y, r1, v, nt, st, itn == 1, c->small + kPart);
+    launch(k_sum_final, 1, 1024, 0, s, c->small + kPart, kDotBlocks, st + S_ALFA);
+    launch(k_y_upd2, nblk(nt), 256, 0, s, y, r2, nt, st);
     AFI_LAUNCH_CHECK();
     double *t = r1; r1 = r2; r2 = y; y = t;
     AFI_TRY(op_precond(c, r2, y, s));
     AFI_TRY(dot(c, r2, y, nt, st + S_BETA2, s));
-    k_minres_scalars<<<1, 1, 0, s>>>(st, tol);
+    launch(k_minres_scalars, 1, 1, 0, s, st, tol);
     // w update uses the rotated buffers: new w overwrites w1's storage
-    k_w_upd<<<nblk(nt), 256, 0, s>>>(v, w1, w2, w1, x, nt, st);
+    launch(k_w_upd, nblk(nt), 256, 0, s, v, w1, w2, w1, x, nt, st);
     AFI_LAUNCH_CHECK();
     double *tw = w1; w1 = w2; w2 = tw;   // (w1, w2) <- (old w2, new w)
     AFI_CUDA(cudaMemcpyAsync(hs, st, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -578,7 +578,7 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
     if (hs[S_FLAG] == 1.0 && itn - last_check >= 5) {
       last_check = itn;
       AFI_TRY(op_saddle(c, x, tmp, s));
-      k_sub<<<nblk(nt), 256, 0, s>>>(b, tmp, tmp, nt);
+      launch(k_sub, nblk(nt), 256, 0, s, b, tmp, tmp, nt);
       AFI_TRY(dot(c, tmp, tmp, nt, st + S_RES2, s));
       AFI_CUDA(cudaMemcpyAsync(hs, st, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
       AFI_CUDA(cudaStreamSynchronize(s));
@@ -590,7 +590,7 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   // true residual of the final iterate if not just measured
   if (last_check != itn) {
     AFI_TRY(op_saddle(c, x, tmp, s));
-    k_sub<<<nblk(nt), 256, 0, s>>>(b, tmp, tmp, nt);
+    launch(k_sub, nblk(nt), 256, 0, s, b, tmp, tmp, nt);
     AFI_TRY(dot(c, tmp, tmp, nt, st + S_RES2, s));
     AFI_CUDA(cudaMemcpyAsync(hs, st, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFI_CUDA(cudaStreamSynchronize(s));
@@ -605,7 +605,7 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
     AFI_TRY(op_dense_inv(c, gbuf(c, 0), gbuf(c, 1), s));
     AFI_TRY(op_R_sub(c, gbuf(c, 1), u, s));
     if (lam_out) {
-      k_add<<<nblk(m), 256, 0, s>>>(lam0, x + n, lam_out, m);
+      launch(k_add, nblk(m), 256, 0, s, lam0, x + n, lam_out, m);
       AFI_LAUNCH_CHECK();
     }
   }

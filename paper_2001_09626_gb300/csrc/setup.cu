@@ -16,6 +16,8 @@
 
 namespace afi {
 
+std::atomic<long long> g_launches{0};
+
 static std::mutex g_err_mu;
 static std::string g_err;
 
@@ -270,7 +272,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   std::vector<double> hctrl(prob->ctrl, prob->ctrl + xoff);
   AFI_TRY(upload(c, &c->ctrl, hctrl));
   AFI_TRY(build_1d_tables(c));
-  k_patch_H<<<NP, 256>>>(c->patches, c->ctrl, D);
+  launch(k_patch_H, NP, 256, 0, 0, c->patches, c->ctrl, D);
   AFI_LAUNCH_CHECK();
   AFI_CUDA(cudaMemcpy(c->hp.data(), c->patches, NP * sizeof(DevPatch), cudaMemcpyDeviceToHost));
   AFI_TRY(dalloc(c, (void **)&c->qgeo, (size_t)(D * D + 1) * qoff * sizeof(double)));
@@ -426,14 +428,14 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     cudaMemcpy(dptr, bptr.data(), bptr.size() * sizeof(int), cudaMemcpyHostToDevice);
     cudaMemcpy(dkk, bkk.data(), bkk.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (!bent.empty()) cudaMemcpy(dent, bent.data(), bent.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    k_rr_blocks<<<ndiag, 256>>>(c->patches, c->ctrl, dptr, dkk, dent, c->GtG, c->ng, nm, D, 0);
+    launch(k_rr_blocks, ndiag, 256, 0, 0, c->patches, c->ctrl, dptr, dkk, dent, c->GtG, c->ng, nm, D, 0);
     int npair = (int)bkk.size() - ndiag;
     if (npair > 0)
-      k_rr_blocks<<<npair, 256>>>(c->patches, c->ctrl, dptr + ndiag, dkk + ndiag, dent, c->GtG, c->ng, nm, D, 1);
+      launch(k_rr_blocks, npair, 256, 0, 0, c->patches, c->ctrl, dptr + ndiag, dkk + ndiag, dent, c->GtG, c->ng, nm, D, 1);
     AFI_LAUNCH_CHECK();
     // R^T R per patch
     AFI_TRY(dalloc(c, (void **)&c->RtR_inv, (size_t)NP * nm * nm * sizeof(double)));
-    k_RtR<<<NP, 256>>>(c->patches, c->ctrl, c->RtR_inv, D, nm);
+    launch(k_RtR, NP, 256, 0, 0, c->patches, c->ctrl, c->RtR_inv, D, nm);
     AFI_LAUNCH_CHECK();
     AFI_TRY(small_inverses(c, c->RtR_inv, nm, NP));
     afi_status st = AFI_OK;

@@ -119,7 +119,7 @@ def test_manufactured_solution_l2_rate():
         e2 = 0.0
         for k, g in enumerate(s.geo):
             Phi0, _, w, cols, det, _ = assembly._geometry_block(g, g.full_q(), g.full_c())
-            xq = Phi0 @ g.X[cols]
+            xq = np.asarray(Phi0 @ g.X[cols])
             uk = u[s.off[k]:s.off[k + 1]].reshape(2, -1)
             uh = np.stack([Phi0 @ uk[0], Phi0 @ uk[1]], axis=1)
             e2 += np.sum(w * abs(det) * np.sum((uh - uex(xq)) ** 2, axis=1))
