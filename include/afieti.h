@@ -176,6 +176,35 @@ afi_status afi_apply(afi_ctx *ctx, afi_operator op, const double *x_dev, double 
  * precision copies of the eigenvectors are built at setup). */
 afi_status afi_set_precision(afi_ctx *ctx, afi_fd_precision prec);
 
+/* Allocation-free fast diagonalization (the paper has no counterpart: this
+ * serves callers that may not allocate device memory where they need a local
+ * solve, e.g. code being recorded into a CUDA graph that must contain no
+ * allocation, real-time loops on a fixed memory budget, or plug-ins whose
+ * host framework owns all device memory).  Computes, for nblk FP64 tensors
+ * of one shape stacked in r and s ([nblk][n3][n2][n1], i1 fastest, device),
+ *     s = (U3 x U2 x U1) Lambda^{-1} (U3 x U2 x U1)^T r,
+ *     Lambda[i1,i2,i3] = scale * (coef[0] D1[i1] + coef[1] D2[i2]
+ *                                 + coef[2] D3[i3] + shift),
+ * i.e. Algorithm 1 with caller-provided eigen data: U_l is n_l x n_l
+ * row-major (row = basis index, column = mode), D_l has n_l entries, all in
+ * device memory; coef is a host array.  For 2D data pass n3 = 1 and
+ * U3 = D3 = NULL.  Example: coef = (c_1, c_2, c_3), shift = 1,
+ * scale = H^{d-2} gives P_A^{inex,-1} of eq. (5.9); shift = 0, scale = 1 and
+ * interior eigen data give eq. (5.10).
+ * Scratch: a file-scope device array of 2^21 doubles (16 MiB) that every GPU
+ * loading the library holds until the process exits; 2 * nblk * n1*n2*n3
+ * must not exceed 2^21, larger requests return AFI_EINVAL without running.
+ * The first call on a device looks up the array's address (with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array, so calls whose executions overlap on the GPU (different streams
+ * or devices' concurrent work on one device) race; every scratch element is
+ * written before it is read, so nothing needs clearing.  Calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Stream-ordered, asynchronous. */
+afi_status afi_fd_apply_static(int n1, int n2, int n3, const double *U1, const double *U2,
+                               const double *U3, const double *D1, const double *D2,
+                               const double *D3, const double coef[3], double shift, double scale,
+                               const double *r, double *s, int nblk, void *stream);
+
 /* n_dof (torn length) and n_c (number of constraints). */
 afi_status afi_sizes(const afi_ctx *ctx, long *n_dof, long *n_c);
 

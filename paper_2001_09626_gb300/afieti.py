@@ -22,7 +22,8 @@ PRECISIONS = {"fp64": AFI_FD_FP64, "fp32": AFI_FD_FP32, "tf32": AFI_FD_TF32, "bf
 
 EXPORTED = ["af_ieti_setup", "fd_apply", "ieti_solve", "ieti_solve_adjoint", "afi_lame_grad",
             "afi_load_vector", "afi_apply", "afi_set_precision", "afi_sizes", "afi_memory",
-            "af_ieti_destroy", "afi_status_string", "afi_last_error", "afi_kernel_launches"]
+            "af_ieti_destroy", "afi_status_string", "afi_last_error", "afi_kernel_launches",
+            "afi_fd_apply_static"]
 
 
 class afi_problem(C.Structure):
@@ -85,6 +86,9 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.afi_status_string.restype = C.c_char_p
     lib.afi_last_error.argtypes = []
     lib.afi_last_error.restype = C.c_char_p
+    lib.afi_fd_apply_static.argtypes = [ip, ip, ip, dp, dp, dp, dp, dp, dp,
+                                         C.POINTER(C.c_double), C.c_double, C.c_double, dp, dp,
+                                         ip, vp]
     lib.afi_kernel_launches.argtypes = []
     lib.afi_kernel_launches.restype = C.c_longlong
     for name in EXPORTED:
@@ -213,6 +217,18 @@ def afi_memory(ctx):
     a, b = C.c_longlong(), C.c_longlong()
     _check(load().afi_memory(C.c_void_p(ctx), C.byref(a), C.byref(b)), "afi_memory")
     return a.value, b.value
+
+
+def afi_fd_apply_static(n, U, D, coef, shift, scale, r, s, nblk=1, stream=None):
+    """Allocation-free FD on nblk tensors of shape n = (n1, n2, n3); U, D are
+    lists of device tensors (U[2], D[2] may be None when n3 == 1)."""
+    cf = (C.c_double * 3)(*[float(x) for x in coef])
+    u3 = _ptr(U[2]) if len(U) > 2 and U[2] is not None else None
+    d3 = _ptr(D[2]) if len(D) > 2 and D[2] is not None else None
+    return _check(load().afi_fd_apply_static(int(n[0]), int(n[1]), int(n[2]), _ptr(U[0]),
+                                             _ptr(U[1]), u3, _ptr(D[0]), _ptr(D[1]), d3, cf,
+                                             float(shift), float(scale), _ptr(r), _ptr(s),
+                                             int(nblk), _stream(stream)), "afi_fd_apply_static")
 
 
 def af_ieti_destroy(ctx):
