@@ -84,7 +84,9 @@ typedef struct {
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
  * preconditioned residual estimate and then the true FP64 residual
  * ||b - A x|| / ||b|| of eq. (4.7) must both reach it); maxit: iteration cap;
- * use_graph, variant: reserved, pass 0. */
+ * use_graph: 1 runs the MINRES iterations as replays of a CUDA graph of six
+ * captured iterations (same iterates and iteration count as 0, which
+ * launches every kernel from the host); variant: reserved, pass 0. */
 typedef struct {
   afi_fd_precision prec;
   double tol;

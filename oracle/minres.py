@@ -4,18 +4,33 @@ Lanczos recurrence with Givens rotations; the solver used by AF-IETI
 residual estimate).  Oracle code: test infrastructure only."""
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 
-def minres(Aop, b, Mop=None, tol=1e-8, maxit=1000, callback=None, true_check=None,
-           check_every=5):
+def next_true_check(itn, true_rel, tol, hist):
+    """Iteration of the next true-residual check after a failed one at `itn`:
+    extrapolate the estimate's mean reduction per iteration over the last five
+    iterations, q = (hist[itn] / hist[itn-5])^(1/5), to the number of
+    iterations that would reduce true_rel to tol; at least 5, at most 50."""
+    extra = 5
+    if itn >= 5 and hist[itn - 5] > 0 and hist[itn] > 0:
+        q = (hist[itn] / hist[itn - 5]) ** 0.2
+        if 0.0 < q < 1.0:
+            extra = math.ceil(math.log(true_rel / tol) / (-math.log(q)))
+    return itn + min(max(extra, 5), 50)
+
+
+def minres(Aop, b, Mop=None, tol=1e-8, maxit=1000, callback=None, true_check=None):
     """Solve A x = b for symmetric A with SPD preconditioner M^{-1} = Mop.
 
     Stops when the recurrence estimate phibar/beta1 of the preconditioned
     residual falls to tol; if ``true_check(x)`` is given (the true relative
     residual ||b - A x|| / ||b||), iterations continue past that point until
-    the true residual is also at or below tol, checked every `check_every`
-    iterations.  Returns (x, info) with info = {iters, relres_est, history}."""
+    the true residual is also at or below tol, re-checked at the iteration
+    given by next_true_check.  Returns (x, info) with info = {iters,
+    relres_est, history}."""
     Mop = Mop or (lambda v: v)
     n = b.shape[0]
     x = np.zeros(n)
@@ -35,7 +50,7 @@ def minres(Aop, b, Mop=None, tol=1e-8, maxit=1000, callback=None, true_check=Non
     r2 = r1.copy()
     hist = [1.0]
     itn = 0
-    last_check = -1
+    next_check = 0
     while itn < maxit:
         itn += 1
         s = 1.0 / beta
@@ -74,8 +89,9 @@ def minres(Aop, b, Mop=None, tol=1e-8, maxit=1000, callback=None, true_check=Non
         if rel <= tol:
             if true_check is None:
                 break
-            if (itn - last_check) >= check_every or last_check < 0:
-                last_check = itn
-                if true_check(x) <= tol:
+            if itn >= next_check:
+                tr = true_check(x)
+                if tr <= tol:
                     break
+                next_check = next_true_check(itn, tr, tol, hist)
     return x, {"iters": itn, "relres_est": float(phibar / beta1), "history": hist}

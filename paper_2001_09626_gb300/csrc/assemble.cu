@@ -232,11 +232,11 @@ __global__ void k_asm3(const DevPatch *P, const int *batch, const Tab1D *tabs,
         }
       }
       const int o = o1 + pt.W[0] * (o2 + pt.W[1] * o3);
-      const long long node = i1 + (long long)n1 * (i2 + (long long)n2 * i3);
+      const long long node = i1 + (long long)pt.n1p * (i2 + (long long)n2 * i3);
       for (int t = 0; t < NLM; ++t) {
         int l, m;
         lm_of(DIM, t, l, m);
-        A[pt.soff + (((long long)(l * DIM + m) * pt.S + o) * pt.N) + node] = acc[t];
+        A[pt.soff + (((long long)(l * DIM + m) * pt.S + o) * pt.NP) + node] = acc[t];
       }
     }
 }
@@ -246,20 +246,21 @@ template <int DIM>
 __global__ void k_asm_fill(const DevPatch *P, double *A) {
   const DevPatch pt = P[blockIdx.y];
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long tot = (long long)pt.S * pt.N;
+  const long long tot = (long long)pt.S * pt.NP;
   if (idx >= tot) return;
-  const int node = (int)(idx % pt.N), o = (int)(idx / pt.N);
-  const int i1 = node % pt.n[0], i2 = (node / pt.n[0]) % pt.n[1], i3 = node / (pt.n[0] * pt.n[1]);
+  const int node = (int)(idx % pt.NP), o = (int)(idx / pt.NP);
+  const int i1 = node % pt.n1p, i2 = (node / pt.n1p) % pt.n[1], i3 = node / (pt.n1p * pt.n[1]);
+  if (i1 >= pt.n[0]) return;   // row padding stays zero
   const int o1 = o % pt.W[0], o2 = (o / pt.W[0]) % pt.W[1], o3 = o / (pt.W[0] * pt.W[1]);
   const int p = pt.p;
   const int j1 = i1 + o1 - p, j2 = i2 + o2 - p, j3 = (DIM == 3) ? i3 + o3 - p : i3;
   const bool valid = j1 >= 0 && j1 < pt.n[0] && j2 >= 0 && j2 < pt.n[1] && j3 >= 0 && j3 < pt.n[2];
   const int orf = (pt.W[0] - 1 - o1) + pt.W[0] * ((pt.W[1] - 1 - o2) + pt.W[1] * (pt.W[2] - 1 - o3));
-  const long long jn = j1 + (long long)pt.n[0] * (j2 + (long long)pt.n[1] * j3);
+  const long long jn = j1 + (long long)pt.n1p * (j2 + (long long)pt.n[1] * j3);
   for (int l = 1; l < DIM; ++l)
     for (int m = 0; m < l; ++m) {
-      double v = valid ? A[pt.soff + ((long long)(m * DIM + l) * pt.S + orf) * pt.N + jn] : 0.0;
-      A[pt.soff + ((long long)(l * DIM + m) * pt.S + o) * pt.N + node] = v;
+      double v = valid ? A[pt.soff + ((long long)(m * DIM + l) * pt.S + orf) * pt.NP + jn] : 0.0;
+      A[pt.soff + ((long long)(l * DIM + m) * pt.S + o) * pt.NP + node] = v;
     }
 }
 
@@ -343,7 +344,7 @@ afi_status assemble_stiffness(afi_ctx *c) {
   }
   if (st == AFI_OK) {
     long long maxSN = 1;
-    for (auto &p : c->hp) maxSN = std::max(maxSN, (long long)p.S * p.N);
+    for (auto &p : c->hp) maxSN = std::max(maxSN, (long long)p.S * p.NP);
     dim3 g((unsigned)((maxSN + 255) / 256), c->npatch);
     if (D == 3) launch(k_asm_fill<3>, g, 256, 0, 0, c->patches, c->stencil);
     else launch(k_asm_fill<2>, g, 256, 0, 0, c->patches, c->stencil);

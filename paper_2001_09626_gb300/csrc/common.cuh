@@ -58,6 +58,10 @@ struct Tab1D {
   long long Ui, Di;            // interior pencil [ni][ni], [ni]
   long long Uf, Uif;           // FP32 copies (float pool)
   long long Ub, Uib;           // BF16 copies (bf16 pool), row-major like U
+  int ld, ldi;                 // padded leading dimensions (multiples of 4)
+  long long Up, Upt;           // U and U^T padded to [n][ld] (zero padding)
+  long long Uip, Uipt;         // interior U and U^T padded to [ni][ldi]
+  long long Kb, Mb;            // bands by diagonal: Kb[t*n + i] = K[i][i + t - p], t = 0..2p
 };
 
 // Per-patch descriptor (device-side POD).
@@ -69,7 +73,7 @@ struct DevPatch {
   int tab[3];       // 1D table per direction
   int p, N, Ni, S;  // degree, nodes, interior nodes, stencil offsets
   int NQ;           // quadrature points of the patch
-  int pad_;
+  int n1p, NP;      // stencil planes: rows padded to even length n1p, NP = n1p*n2*n3
   long long off;    // torn offset of component 0
   long long ioff;   // compact interior offset of component 0
   long long soff;   // stiffness stencil offset (doubles)
@@ -94,6 +98,7 @@ struct afi_ctx {
   std::vector<afi::DevPatch> hp;
   std::vector<afi::Tab1D> htab;
   int max_N = 0, max_n = 0;
+  int smem_optin = 0;                // opt-in dynamic shared memory per block
 
   // device data
   afi::DevPatch *patches = nullptr;
@@ -128,17 +133,25 @@ struct afi_ctx {
   double *ws = nullptr; long long ws_n = 0;     // general FP64 workspace
   double *fdscratch = nullptr; long long fdscratch_n = 0;
   double *small = nullptr;                      // reduction / scalar area
+  double *part = nullptr;                       // per-patch partial sums
   double *host_small = nullptr;                 // pinned host mirror
   int *dflag = nullptr;
 
   long long bytes = 0;
+
+  // captured MINRES iterations (cudaGraphExec_t), rebuilt when prec changes
+  void *graph_exec = nullptr;
+  void *cap_stream = nullptr;        // private stream used only for capture
+  const double *gate = nullptr;      // while enqueueing MINRES: device 'active' flag
+  long long graph_nodes = 0;
+  int graph_prec = -1;
 };
 
 namespace afi {
 
 constexpr int kSmallDoubles = 1 << 16;   // reduction scratch (partials + scalars)
 constexpr int kOpScratch = 5;            // operator scratch, in units of (n_dof + n_c)
-constexpr int kKrylov = 11;              // MINRES vectors of length n_dof + n_c
+constexpr int kKrylov = 12;              // MINRES vectors of length n_dof + n_c
 
 // allocation helper that records bytes
 afi_status dalloc(afi_ctx *c, void **p, size_t bytes);
@@ -174,6 +187,9 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam, afi_in
 afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st);
 afi_status schur_run(afi_ctx *c, const double *t, double *y, cudaStream_t st);
 afi_status fd_prepare(afi_ctx *c);
+// fd_tc.cu (tensor-core FD; AFI_EINVAL if a patch tensor does not fit)
+afi_status fd_tc_prepare(afi_ctx *c);
+afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st);
 
 // reductions (ops.cu)
 afi_status dot(afi_ctx *c, const double *a, const double *b, long n, double *dst,

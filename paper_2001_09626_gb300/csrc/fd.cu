@@ -10,6 +10,10 @@
 // One CTA owns one (patch, component) tensor; the tensor lives in shared
 // memory when it fits and in a global scratch slab otherwise.  Arithmetic is
 // FP64 (plain form) or FP32 (mixed form), inputs and outputs FP64.
+//
+// Mode products are register blocked: a thread computes RA = 4 consecutive
+// outputs of one line, loading each input once and the 4 coefficients of a
+// row of the (zero-padded) U or U^T copy with one vector load.
 #include "common.cuh"
 
 namespace afi {
@@ -18,50 +22,81 @@ template <typename T> struct Pool;
 template <> struct Pool<double> { static const double *get(const afi_ctx *c) { return c->dpool; } };
 template <> struct Pool<float> { static const float *get(const afi_ctx *c) { return c->fpool; } };
 
-// dst = op(U) applied along direction d.  TRANS: dst[a] = sum_i U[i][a] src[i]
-// (forward transform), else dst[i] = sum_a U[i][a] src[a].
-template <typename T, bool TRANS>
-__device__ __forceinline__ void mode_dense(const T *__restrict__ src, T *__restrict__ dst,
-                                           const T *__restrict__ U, int n, int d, int n1, int n2,
-                                           int n3) {
-  const int tot = n1 * n2 * n3;
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+  static __device__ __forceinline__ void load(const float *p, float *o) {
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <> struct Vec4<double> {
+  static __device__ __forceinline__ void load(const double *p, double *o) {
+    double2 a = *reinterpret_cast<const double2 *>(p), b = *reinterpret_cast<const double2 *>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+  }
+};
+
+constexpr int RA = 4;
+
+// dst[.., a, ..] = sum_j Mp[j][a] src[.., j, ..] along direction d, Mp padded
+// to leading dimension ld (multiple of 4).  Forward transforms pass U
+// (Mp[j][a] = U[j][a]); back transforms pass U^T.
+template <typename T>
+__device__ __forceinline__ void mode_rb(const T *__restrict__ src, T *__restrict__ dst,
+                                        const T *__restrict__ Mp, int ld, int n, int d, int n1,
+                                        int n2, int n3) {
+  const int N = n1 * n2 * n3;
+  const int nl = N / n, nab = (n + RA - 1) / RA;
   const int stride = (d == 0) ? 1 : (d == 1 ? n1 : n1 * n2);
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int io = (d == 0) ? idx % n1 : (d == 1 ? (idx / n1) % n2 : idx / (n1 * n2));
-    const T *base = src + idx - io * stride;
-    T acc = 0;
-    if (TRANS) {
-#pragma unroll 4
-      for (int j = 0; j < n; ++j) acc += U[j * n + io] * base[j * stride];
-    } else {
-      const T *row = U + io * n;
-#pragma unroll 4
-      for (int j = 0; j < n; ++j) acc += row[j] * base[j * stride];
+  for (int item = threadIdx.x; item < nl * nab; item += blockDim.x) {
+    const int line = item % nl, a0 = (item / nl) * RA;
+    int base;
+    if (d == 0) base = line * n1;
+    else if (d == 1) base = (line % n1) + (line / n1) * n1 * n2;
+    else base = line;
+    T acc[RA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) acc[r] = T(0);
+    const T *row = Mp + a0;
+    for (int j = 0; j < n; ++j) {
+      const T x = src[base + j * stride];
+      T m[RA];
+      Vec4<T>::load(row + j * ld, m);
+#pragma unroll
+      for (int r = 0; r < RA; ++r) acc[r] += m[r] * x;
     }
-    dst[idx] = acc;
+#pragma unroll
+    for (int r = 0; r < RA; ++r)
+      if (a0 + r < n) dst[base + (a0 + r) * stride] = acc[r];
   }
 }
 
 // dst = alpha * Mat1(src1) [+ beta * Mat2(src2)] along direction d, with the
-// banded (half-bandwidth p) n x n matrices of the univariate pencil.
+// banded (half-bandwidth p) univariate matrices stored by diagonal:
+// Mb[t*n + i] = Mat[i][i + t - p].
 template <typename T>
-__device__ __forceinline__ void mode_band2(const T *__restrict__ src1, const T *__restrict__ M1,
+__device__ __forceinline__ void mode_band2(const T *__restrict__ src1, const T *__restrict__ Mb1,
                                            T alpha, const T *__restrict__ src2,
-                                           const T *__restrict__ M2, T beta, T *__restrict__ dst,
+                                           const T *__restrict__ Mb2, T beta, T *__restrict__ dst,
                                            int p, int d, int n1, int n2, int n3) {
   const int tot = n1 * n2 * n3;
   const int n = (d == 0) ? n1 : (d == 1 ? n2 : n3);
   const int stride = (d == 0) ? 1 : (d == 1 ? n1 : n1 * n2);
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int io = (d == 0) ? idx % n1 : (d == 1 ? (idx / n1) % n2 : idx / (n1 * n2));
-    const int lo = max(io - p, 0), hi = min(io + p, n - 1);
-    const long long base = idx - (long long)io * stride;
+    const int tlo = max(p - io, 0), thi = min(2 * p, p + n - 1 - io);
+    const int base = idx + (-p) * stride;   // element j = io + t - p sits at base + t*stride
     T a1 = 0, a2 = 0;
-    for (int j = lo; j <= hi; ++j) {
-      a1 += M1[io * n + j] * src1[base + (long long)j * stride];
-      if (src2) a2 += M2[io * n + j] * src2[base + (long long)j * stride];
+    if (src2) {
+      for (int t = tlo; t <= thi; ++t) {
+        a1 += Mb1[t * n + io] * src1[base + t * stride];
+        a2 += Mb2[t * n + io] * src2[base + t * stride];
+      }
+      dst[idx] = alpha * a1 + beta * a2;
+    } else {
+      for (int t = tlo; t <= thi; ++t) a1 += Mb1[t * n + io] * src1[base + t * stride];
+      dst[idx] = alpha * a1;
     }
-    dst[idx] = alpha * a1 + (src2 ? beta * a2 : T(0));
   }
 }
 
@@ -74,114 +109,86 @@ __device__ __forceinline__ Dims dims_of(const DevPatch &pt, int interior) {
   return D;
 }
 
-// Algorithm 1 on the tensor in `cur` (ping-pong with `oth`).  The final mode
-// product goes to `dst` (FP64, contiguous) or, if scatter_full is given, is
-// negated and scattered to the interior positions of a full patch tensor
-// (the interior solve inside the Schur complement).
+// Algorithm 1 on the tensor in `cur` (ping-pong with `oth`).  Returns the
+// buffer that holds the result.
 template <typename T>
-__device__ void fd_tensor(T *cur, T *oth, const DevPatch &pt, const Tab1D *tabs,
-                          const double *dpool, const T *upool, int dim, int l, int interior,
-                          double *dst, T *scatter_full) {
+__device__ T *fd_tensor(T *cur, T *oth, const DevPatch &pt, const Tab1D *tabs, const T *tpool,
+                        int dim, int l, int interior) {
   const Dims D = dims_of(pt, interior);
-  const T *U[3];
-  const double *Dv[3];
+  const T *Uf[3], *Ub[3], *Dv[3];
+  int ld[3];
   for (int d = 0; d < 3; ++d) {
     const Tab1D tb = tabs[pt.tab[d]];
-    U[d] = upool + (interior ? tb.Ui : tb.U);
-    Dv[d] = dpool + (interior ? tb.Di : tb.D);
+    Uf[d] = tpool + (interior ? tb.Uip : tb.Up);
+    Ub[d] = tpool + (interior ? tb.Uipt : tb.Upt);
+    Dv[d] = tpool + (interior ? tb.Di : tb.D);
+    ld[d] = interior ? tb.ldi : tb.ld;
   }
-  // forward: r~ = (U^T x ... x U^T) r
-  for (int d = 0; d < dim; ++d) {
-    mode_dense<T, true>(cur, oth, U[d], D.n[d], d, D.n[0], D.n[1], D.n[2]);
+  for (int d = 0; d < dim; ++d) {   // r~ = (U^T x ... x U^T) r
+    mode_rb<T>(cur, oth, Uf[d], ld[d], D.n[d], d, D.n[0], D.n[1], D.n[2]);
     __syncthreads();
     T *t = cur; cur = oth; oth = t;
   }
-  // scale by Lambda^{-1}
-  const double cl = 2.0 * pt.mu + pt.lam;
-  const double c0 = (l == 0) ? cl : pt.mu, c1 = (l == 1) ? cl : pt.mu, c2 = (l == 2) ? cl : pt.mu;
-  for (int idx = threadIdx.x; idx < D.N; idx += blockDim.x) {
+  const T cl = (T)(2.0 * pt.mu + pt.lam), mu = (T)pt.mu, hs = (T)pt.Hs;
+  const T c0 = (l == 0) ? cl : mu, c1 = (l == 1) ? cl : mu, c2 = (l == 2) ? cl : mu;
+  for (int idx = threadIdx.x; idx < D.N; idx += blockDim.x) {   // q~ = Lambda^{-1} r~
     const int i1 = idx % D.n[0], i2 = (idx / D.n[0]) % D.n[1], i3 = idx / (D.n[0] * D.n[1]);
-    double lam = c0 * Dv[0][i1] + c1 * Dv[1][i2] + (dim == 3 ? c2 * Dv[2][i3] : 0.0);
-    if (!interior) lam = pt.Hs * (lam + 1.0);
-    cur[idx] = (T)((double)cur[idx] / lam);
+    T lam = c0 * Dv[0][i1] + c1 * Dv[1][i2] + (dim == 3 ? c2 * Dv[2][i3] : T(0));
+    if (!interior) lam = hs * (lam + T(1));
+    cur[idx] = cur[idx] / lam;
   }
   __syncthreads();
-  // back: s = (U x ... x U) q~, last direction first
-  for (int d = dim - 1; d >= 1; --d) {
-    mode_dense<T, false>(cur, oth, U[d], D.n[d], d, D.n[0], D.n[1], D.n[2]);
+  for (int d = dim - 1; d >= 0; --d) {   // s = (U x ... x U) q~
+    mode_rb<T>(cur, oth, Ub[d], ld[d], D.n[d], d, D.n[0], D.n[1], D.n[2]);
     __syncthreads();
     T *t = cur; cur = oth; oth = t;
   }
-  // direction 1 straight to the destination
-  const T *U0 = U[0];
-  const int n0 = D.n[0];
-  for (int idx = threadIdx.x; idx < D.N; idx += blockDim.x) {
-    const int io = idx % n0;
-    const T *base = cur + idx - io;
-    const T *row = U0 + io * n0;
-    T acc = 0;
-    for (int j = 0; j < n0; ++j) acc += row[j] * base[j];
-    if (scatter_full) {
-      const int i2 = (idx / n0) % D.n[1], i3 = idx / (n0 * D.n[1]);
-      const int full = (io + 1) + pt.n[0] * ((i2 + 1) + pt.n[1] * (i3 + (dim == 3 ? 1 : 0)));
-      scatter_full[full] = -acc;
-    } else {
-      dst[idx] = (double)acc;
-    }
-  }
-  __syncthreads();
+  return cur;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_fd(const DevPatch *P, const Tab1D *tabs,
-                                            const double *dpool, const T *upool, int dim,
-                                            int interior, const double *r, double *s,
-                                            T *gscratch, int use_smem) {
+__global__ void __launch_bounds__(512) k_fd(const DevPatch *P, const Tab1D *tabs, const T *tpool,
+                                            int dim, int interior, const double *r, double *s,
+                                            T *gscratch, int use_smem, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   extern __shared__ __align__(16) unsigned char smraw[];
   const int k = blockIdx.x, l = blockIdx.y;
   const DevPatch pt = P[k];
   const Dims D = dims_of(pt, interior);
   const long long base = (interior ? pt.ioff : pt.off) + (long long)l * D.N;
-  T *b0, *b1;
-  if (use_smem) {
-    b0 = reinterpret_cast<T *>(smraw);
-    b1 = b0 + D.N;
-  } else {
-    b0 = gscratch + 2 * base;
-    b1 = b0 + D.N;
-  }
+  T *b0 = use_smem ? reinterpret_cast<T *>(smraw) : gscratch + 2 * base;
+  T *b1 = b0 + D.N;
   for (int i = threadIdx.x; i < D.N; i += blockDim.x) b0[i] = (T)r[base + i];
   __syncthreads();
-  fd_tensor<T>(b0, b1, pt, tabs, dpool, upool, dim, l, interior, s + base, nullptr);
+  const T *res = fd_tensor<T>(b0, b1, pt, tabs, tpool, dim, l, interior);
+  for (int i = threadIdx.x; i < D.N; i += blockDim.x) s[base + i] = (double)res[i];
 }
 
 // A_hat_l v (Kronecker form) from buffer v into `out`, using two temporaries.
 template <typename T>
 __device__ void ahat_apply(const T *v, T *out, T *t1, T *t2, const DevPatch &pt,
-                           const Tab1D *tabs, const T *upool, int dim, int l) {
+                           const Tab1D *tabs, const T *tpool, int dim, int l) {
   const int n1 = pt.n[0], n2 = pt.n[1], n3 = pt.n[2];
   const Tab1D A0 = tabs[pt.tab[0]], A1 = tabs[pt.tab[1]], A2 = tabs[pt.tab[2]];
   const T cl = (T)(2.0 * pt.mu + pt.lam), mu = (T)pt.mu;
   const T c0 = (l == 0) ? cl : mu, c1 = (l == 1) ? cl : mu, c2 = (l == 2) ? cl : mu;
   const int p = pt.p;
-  // t1 = M1 v (dir 0), t2 = K1 v (dir 0): done as one pass each
-  mode_band2<T>(v, upool + A0.M, T(1), nullptr, nullptr, T(0), t1, p, 0, n1, n2, n3);
-  mode_band2<T>(v, upool + A0.K, T(1), nullptr, nullptr, T(0), t2, p, 0, n1, n2, n3);
+  // t1 = M_1 v, t2 = K_1 v (direction 1)
+  mode_band2<T>(v, tpool + A0.Mb, T(1), nullptr, nullptr, T(0), t1, p, 0, n1, n2, n3);
+  mode_band2<T>(v, tpool + A0.Kb, T(1), nullptr, nullptr, T(0), t2, p, 0, n1, n2, n3);
   __syncthreads();
-  if (dim == 2) {
-    // out = c0 M2 (K1 v) + c1 K2 (M1 v)
-    mode_band2<T>(t2, upool + A1.M, c0, t1, upool + A1.K, c1, out, p, 1, n1, n2, n3);
+  if (dim == 2) {   // out = c0 M_2 K_1 v + c1 K_2 M_1 v
+    mode_band2<T>(t2, tpool + A1.Mb, c0, t1, tpool + A1.Kb, c1, out, p, 1, n1, n2, n3);
     __syncthreads();
     return;
   }
-  // out = Ta = c0 M2 t2 + c1 K2 t1  (dir 1)
-  mode_band2<T>(t2, upool + A1.M, c0, t1, upool + A1.K, c1, out, p, 1, n1, n2, n3);
+  // out = Ta = c0 M_2 t2 + c1 K_2 t1, then t2 = Tb = M_2 t1 (direction 2)
+  mode_band2<T>(t2, tpool + A1.Mb, c0, t1, tpool + A1.Kb, c1, out, p, 1, n1, n2, n3);
   __syncthreads();
-  // t2 = Tb = M2 t1 (dir 1)
-  mode_band2<T>(t1, upool + A1.M, T(1), nullptr, nullptr, T(0), t2, p, 1, n1, n2, n3);
+  mode_band2<T>(t1, tpool + A1.Mb, T(1), nullptr, nullptr, T(0), t2, p, 1, n1, n2, n3);
   __syncthreads();
-  // t1 = M3 Ta + c2 K3 Tb (dir 2)
-  mode_band2<T>(out, upool + A2.M, T(1), t2, upool + A2.K, c2, t1, p, 2, n1, n2, n3);
+  // t1 = M_3 Ta + c2 K_3 Tb (direction 3), copied to out
+  mode_band2<T>(out, tpool + A2.Mb, T(1), t2, tpool + A2.Kb, c2, t1, p, 2, n1, n2, n3);
   __syncthreads();
   for (int i = threadIdx.x; i < n1 * n2 * n3; i += blockDim.x) out[i] = t1[i];
   __syncthreads();
@@ -197,46 +204,54 @@ __device__ __forceinline__ bool on_shell(int idx, const DevPatch &pt, int dim) {
 // y = H^{d-2} S_hat_l theta for every (patch, component); t, y torn vectors,
 // only shell entries of t are read, interior entries of y are zero.
 template <typename T>
-__global__ void __launch_bounds__(256) k_schur(const DevPatch *P, const Tab1D *tabs,
-                                               const double *dpool, const T *upool, int dim,
-                                               const double *t, double *y, T *gscratch,
-                                               int use_smem) {
+__global__ void __launch_bounds__(512) k_schur(const DevPatch *P, const Tab1D *tabs,
+                                               const T *tpool, int dim, const double *t, double *y,
+                                               T *gscratch, int use_smem, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   extern __shared__ __align__(16) unsigned char smraw[];
   const int k = blockIdx.x, l = blockIdx.y;
   const DevPatch pt = P[k];
   const int N = pt.N;
   const long long base = pt.off + (long long)l * N;
-  T *B0;
-  if (use_smem) B0 = reinterpret_cast<T *>(smraw);
-  else B0 = gscratch + 4 * base;
+  T *B0 = use_smem ? reinterpret_cast<T *>(smraw) : gscratch + 4 * base;
   T *B1 = B0 + N, *B2 = B1 + N, *B3 = B2 + N;
   for (int i = threadIdx.x; i < N; i += blockDim.x)
     B0[i] = on_shell(i, pt, dim) ? (T)t[base + i] : T(0);
   __syncthreads();
-  // first product: out = A_hat [theta; 0]
-  T *out = B1;
-  ahat_apply<T>(B0, out, B2, B3, pt, tabs, upool, dim, l);
-  // interior solve v_I = -(A_hat)_II^{-1} out_I, compact in B2/B3
-  Dims Di = dims_of(pt, 1);
+  ahat_apply<T>(B0, B1, B2, B3, pt, tabs, tpool, dim, l);   // B1 = A_hat [theta; 0]
+  // interior solve v_I = -(A_hat)_II^{-1} (B1)_I on compact tensors in B2/B3
+  const Dims Di = dims_of(pt, 1);
+  const int zoff = (dim == 3) ? 1 : 0;
   for (int idx = threadIdx.x; idx < Di.N; idx += blockDim.x) {
     const int j1 = idx % Di.n[0], j2 = (idx / Di.n[0]) % Di.n[1], j3 = idx / (Di.n[0] * Di.n[1]);
-    const int full = (j1 + 1) + pt.n[0] * ((j2 + 1) + pt.n[1] * (j3 + (dim == 3 ? 1 : 0)));
-    B2[idx] = out[full];
+    B2[idx] = B1[(j1 + 1) + pt.n[0] * ((j2 + 1) + pt.n[1] * (j3 + zoff))];
   }
   __syncthreads();
-  fd_tensor<T>(B2, B3, pt, tabs, dpool, upool, dim, l, 1, nullptr, B0);
-  // second product on [theta; v_I]
-  ahat_apply<T>(B0, out, B2, B3, pt, tabs, upool, dim, l);
+  const T *vI = fd_tensor<T>(B2, B3, pt, tabs, tpool, dim, l, 1);
+  for (int idx = threadIdx.x; idx < Di.N; idx += blockDim.x) {
+    const int j1 = idx % Di.n[0], j2 = (idx / Di.n[0]) % Di.n[1], j3 = idx / (Di.n[0] * Di.n[1]);
+    B0[(j1 + 1) + pt.n[0] * ((j2 + 1) + pt.n[1] * (j3 + zoff))] = -vI[idx];
+  }
+  __syncthreads();
+  ahat_apply<T>(B0, B1, B2, B3, pt, tabs, tpool, dim, l);   // B1 = A_hat [theta; v_I]
   const double hs = pt.Hs;
   for (int i = threadIdx.x; i < N; i += blockDim.x)
-    y[base + i] = on_shell(i, pt, dim) ? hs * (double)out[i] : 0.0;
+    y[base + i] = on_shell(i, pt, dim) ? hs * (double)B1[i] : 0.0;
 }
 
-static int smem_limit() {
+// Opt the local-solver kernels into the device's full dynamic shared memory
+// once per context (outside any stream capture).
+afi_status fd_prepare(afi_ctx *c) {
   int dev = 0, v = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  return v;
+  AFI_CUDA(cudaGetDevice(&dev));
+  AFI_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  c->smem_optin = v;
+  // these kernels have no static shared memory: the whole opt-in size is dynamic
+  AFI_CUDA(cudaFuncSetAttribute(k_fd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  AFI_CUDA(cudaFuncSetAttribute(k_fd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  AFI_CUDA(cudaFuncSetAttribute(k_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  AFI_CUDA(cudaFuncSetAttribute(k_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
+  return AFI_OK;
 }
 
 template <typename T>
@@ -244,12 +259,11 @@ static afi_status fd_launch(afi_ctx *c, int interior, const double *r, double *s
   int maxN = 1;
   for (auto &p : c->hp) maxN = std::max(maxN, interior ? p.Ni : p.N);
   size_t smem = 2ull * maxN * sizeof(T);
-  int use_smem = smem <= (size_t)smem_limit();
-  if (use_smem) AFI_CUDA(cudaFuncSetAttribute(k_fd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  else smem = 0;
-  launch(k_fd<T>, dim3(c->npatch, c->dim), 256, smem, st, c->patches, c->tabs, c->dpool, Pool<T>::get(c),
-                                                     c->dim, interior, r, s,
-                                                     reinterpret_cast<T *>(c->fdscratch), use_smem);
+  const int use_smem = smem <= (size_t)c->smem_optin;
+  if (!use_smem) smem = 0;
+  launch(k_fd<T>, dim3(c->npatch, c->dim), 512, smem, st, c->patches, (const Tab1D *)c->tabs,
+         Pool<T>::get(c), c->dim, interior, r, s, reinterpret_cast<T *>(c->fdscratch), use_smem,
+         (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -257,12 +271,11 @@ static afi_status fd_launch(afi_ctx *c, int interior, const double *r, double *s
 template <typename T>
 static afi_status schur_launch(afi_ctx *c, const double *t, double *y, cudaStream_t st) {
   size_t smem = 4ull * c->max_N * sizeof(T);
-  int use_smem = smem <= (size_t)smem_limit();
-  if (use_smem) AFI_CUDA(cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  else smem = 0;
-  launch(k_schur<T>, dim3(c->npatch, c->dim), 256, smem, st, c->patches, c->tabs, c->dpool, Pool<T>::get(c),
-                                                         c->dim, t, y,
-                                                         reinterpret_cast<T *>(c->fdscratch), use_smem);
+  const int use_smem = smem <= (size_t)c->smem_optin;
+  if (!use_smem) smem = 0;
+  launch(k_schur<T>, dim3(c->npatch, c->dim), 512, smem, st, c->patches, (const Tab1D *)c->tabs,
+         Pool<T>::get(c), c->dim, t, y, reinterpret_cast<T *>(c->fdscratch), use_smem,
+         (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -271,16 +284,21 @@ afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStre
   switch (c->opt.prec) {
     case AFI_FD_FP64: return fd_launch<double>(c, interior, r, s, st);
     case AFI_FD_FP32: return fd_launch<float>(c, interior, r, s, st);
+    case AFI_FD_TF32:
+    case AFI_FD_BF16:
+      // tensor cores when every patch tensor fits the single-CTA kernel,
+      // FP32 otherwise
+      if (fd_tc_run(c, interior, r, s, st) == AFI_OK) return AFI_OK;
+      return fd_launch<float>(c, interior, r, s, st);
     default: set_error("local-solver precision not available"); return AFI_EINVAL;
   }
 }
 
+// The Schur block (banded A_hat products and the interior FD between them)
+// runs in FP64 for the plain form and in FP32 for every mixed form.
 afi_status schur_run(afi_ctx *c, const double *t, double *y, cudaStream_t st) {
-  switch (c->opt.prec) {
-    case AFI_FD_FP64: return schur_launch<double>(c, t, y, st);
-    case AFI_FD_FP32: return schur_launch<float>(c, t, y, st);
-    default: set_error("local-solver precision not available"); return AFI_EINVAL;
-  }
+  if (c->opt.prec == AFI_FD_FP64) return schur_launch<double>(c, t, y, st);
+  return schur_launch<float>(c, t, y, st);
 }
 
 }  // namespace afi

@@ -1,0 +1,306 @@
+// Fast diagonalization (Algorithm 1, eqs. 5.6, 5.9, 5.10) on the 5th
+// generation tensor cores: tcgen05.mma with TF32 or BF16 operands in shared
+// memory and FP32 accumulators in tensor memory.
+//
+// One CTA owns one (patch, component) tensor X[i3][i2][i1].  Each of the six
+// mode products (U_1^T, U_2^T, U_3^T, then U_1, U_2, U_3) is a GEMM
+//     D[line][a] = sum_k A[line][k] B[a][k],
+// where the rows ("lines") run over the two uncontracted indices and k over
+// the contracted one, which is always the fastest index of the operand: the
+// epilogue of every mode writes its result with the axes rotated
+// ([c][b][a] -> [a'][c][b]), so the next contraction is again over the
+// contiguous index and A stays K-major.  After three rotations the axes are
+// back in their original order.  The scaling by Lambda^{-1} is fused into the
+// epilogue of the third product, and the last epilogue writes FP64 straight
+// to global memory.
+//
+// Operands use the no-swizzle K-major canonical layout of core matrices
+// (8 rows x 16 bytes); one elected thread issues the MMAs (M = 128 lines per
+// tile, N = output modes padded to 16, K in steps of 32 bytes) and commits
+// them to an mbarrier that all threads wait on with a bounded spin.
+#include "common.cuh"
+
+namespace afi {
+
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: FP32 accumulate, A/B format fmt (2 = TF32, 1 = BF16),
+// both K-major, N and M dimensions
+__device__ __forceinline__ uint32_t idesc(int fmt, int M, int N) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+template <int FMT>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  if (FMT == 2)
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d), "l"(a),
+                 "l"(b), "r"(id), "r"(acc));
+  else
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d), "l"(a),
+                 "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint64_t *mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+      smem_u32(mbar)));
+}
+
+// bounded wait for the given phase of an mbarrier; false on timeout
+__device__ __forceinline__ bool wait_phase(uint64_t *mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it)
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(smem_u32(mbar)), "r"(phase));
+  return done != 0;
+}
+
+__device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+                 "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int FMT> struct Op;
+template <> struct Op<2> {   // TF32: FP32 storage, 4 elements per 16 bytes, 8 per MMA
+  using T = float;
+  static constexpr int T16 = 4, KSTEP = 8;
+  static __device__ __forceinline__ T cvt(float x) { return x; }
+};
+template <> struct Op<1> {   // BF16: 8 elements per 16 bytes, 16 per MMA
+  using T = __nv_bfloat16;
+  static constexpr int T16 = 8, KSTEP = 16;
+  static __device__ __forceinline__ T cvt(float x) { return __float2bfloat16(x); }
+};
+
+__host__ __device__ __forceinline__ int rup(int x, int m) { return (x + m - 1) / m * m; }
+
+// element offset of (row, k) in the K-major core-matrix layout with Kp columns
+template <int FMT>
+__device__ __forceinline__ int cm(int row, int k, int Kp) {
+  constexpr int T16 = Op<FMT>::T16;
+  return (((row >> 3) * (Kp / T16) + k / T16) * 8 + (row & 7)) * T16 + (k % T16);
+}
+
+}  // namespace tc
+
+template <int FMT>
+__global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *tabs,
+                                               const float *fpool, int dim, int interior,
+                                               const double *r, double *s, int cap, int bsz,
+                                               int tcols, const double *gate, int *err) {
+  using namespace tc;
+  using T = typename Op<FMT>::T;
+  constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
+  if (gate && *gate == 0.0) return;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ int failed;
+  T *buf[2] = {reinterpret_cast<T *>(smraw), reinterpret_cast<T *>(smraw) + cap};
+  T *bm = reinterpret_cast<T *>(smraw) + 2 * cap;   // 6 B operands, bsz elements each
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int k = blockIdx.x, l = blockIdx.y;
+  const DevPatch pt = P[k];
+  int n[3];
+  for (int d = 0; d < 3; ++d) n[d] = interior ? pt.ni[d] : pt.n[d];
+  const int N = n[0] * n[1] * n[2];
+  const long long base = (interior ? pt.ioff : pt.off) + (long long)l * N;
+
+  // zero both operand buffers, build the six B operands from U
+  for (int i = tid; i < 2 * cap; i += blockDim.x) buf[0][i] = Op<FMT>::cvt(0.f);
+  for (int m = 0; m < 6; ++m) {
+    const int d = m % 3;
+    const Tab1D tb = tabs[pt.tab[d]];
+    const float *U = fpool + (interior ? tb.Ui : tb.U);
+    const int nd = n[d], Kp = rup(nd, KSTEP), Np = rup(nd, 16);
+    T *B = bm + m * bsz;
+    for (int i = tid; i < Np * Kp; i += blockDim.x) {
+      const int a = i / Kp, kk = i % Kp;
+      float v = 0.f;
+      if (a < nd && kk < nd) v = (m < 3) ? U[kk * nd + a] : U[a * nd + kk];
+      B[cm<FMT>(a, kk, Kp)] = Op<FMT>::cvt(v);
+    }
+  }
+  __syncthreads();
+  // load the tensor as the first operand: line = i2 + n2 i3, k = i1
+  {
+    const int Kp = rup(n[0], KSTEP);
+    for (int idx = tid; idx < N; idx += blockDim.x)
+      buf[0][cm<FMT>(idx / n[0], idx % n[0], Kp)] = Op<FMT>::cvt((float)r[base + idx]);
+  }
+  if (tid == 0) {
+    failed = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+
+  // Lambda for this (patch, component)
+  const float cl = (float)(2.0 * pt.mu + pt.lam), mu = (float)pt.mu, hs = (float)pt.Hs;
+  const float c0 = (l == 0) ? cl : mu, c1 = (l == 1) ? cl : mu, c2 = (l == 2) ? cl : mu;
+  const float *Dv[3];
+  for (int d = 0; d < 3; ++d) {
+    const Tab1D tb = tabs[pt.tab[d]];
+    Dv[d] = fpool + (interior ? tb.Di : tb.D);
+  }
+
+  int na = n[0], nb = n[1], nc = n[2];   // current operand dims, a fastest
+  for (int m = 0; m < 6; ++m) {
+    const int L = nb * nc, ntile = rup(L, 128) / 128;
+    const int Kp = rup(na, KSTEP), Np = rup(na, 16);
+    T *A = buf[m & 1];
+    if (tid == 0 && !failed) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t id = idesc(FMT, 128, Np);
+      const uint32_t sbo = (uint32_t)(Kp / T16) * 128u;
+      const uint32_t a0 = smem_u32(A), b0 = smem_u32(bm + m * bsz);
+      for (int t = 0; t < ntile; ++t)
+        for (int ks = 0; ks < Kp / KSTEP; ++ks)
+          mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 16 * sbo + ks * 256, 128, sbo),
+                   sdesc(b0 + ks * 256, 128, sbo), id, ks > 0 ? 1u : 0u);
+      commit(&mbar);
+    }
+    if (!wait_phase(&mbar, (uint32_t)(m & 1))) failed = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (failed) break;
+    // epilogue: D[line][j] -> next operand (rotated) or the FP64 output
+    const int q = warp & 3, half = warp >> 2;
+    const int nnb = nc, nKp = rup(nb, KSTEP);   // next operand: K = nb, lines = nc * na
+    T *An = buf[(m + 1) & 1];
+    for (int t = 0; t < ntile; ++t) {
+      const int line = t * 128 + q * 32 + lane;
+      const int b = line % nb, c = line / nb;
+      for (int j0 = half * 16; j0 < Np; j0 += 32) {
+        float v[16];
+        ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), v);
+        if (line >= L) continue;
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = j0 + jj;
+          if (j >= na) continue;
+          float x = v[jj];
+          if (m == 2) {   // element r~(a1 = b, a2 = c, a3 = j): scale by Lambda^{-1}
+            float lam = c0 * Dv[0][b] + c1 * Dv[1][c] + c2 * Dv[2][j];
+            if (dim != 3) lam = c0 * Dv[0][b] + c1 * Dv[1][c];
+            if (!interior) lam = hs * (lam + 1.f);
+            x = x / lam;
+          }
+          if (m == 5) s[base + b + (long long)n[0] * (c + (long long)n[1] * j)] = (double)x;
+          else An[cm<FMT>(c + nnb * j, b, nKp)] = Op<FMT>::cvt(x);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    // rotate dims: (na, nb, nc) -> (nb, nc, na)
+    const int t0 = na;
+    na = nb; nb = nc; nc = t0;
+  }
+  if (failed) {   // give MMAs still in flight one more bounded wait before freeing TMEM
+    for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+  }
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+  if (tid == 0 && failed) atomicExch(err, 1);
+}
+
+static int g_tc_dyn_max;
+
+// Launch geometry of the tensor-core FD for the context's patches; false if
+// some patch does not fit (the caller then uses the SIMT kernels).
+struct TcPlan { int cap, bsz, tcols; size_t smem; bool ok; };
+
+static TcPlan tc_plan(const afi_ctx *c, int interior, int fmt) {
+  const int kstep = (fmt == 2) ? 8 : 16, esz = (fmt == 2) ? 4 : 2;
+  TcPlan pl{0, 0, 32, 0, true};
+  for (const auto &p : c->hp) {
+    int n[3];
+    for (int d = 0; d < 3; ++d) n[d] = interior ? p.ni[d] : p.n[d];
+    for (int d = 0; d < 3; ++d) {
+      const int na = n[d], nb = n[(d + 1) % 3], nc = n[(d + 2) % 3];
+      const int Lp = tc::rup(nb * nc, 128), Kp = tc::rup(na, kstep), Np = tc::rup(na, 16);
+      pl.cap = std::max(pl.cap, Lp * Kp);
+      pl.bsz = std::max(pl.bsz, Np * Kp);
+      int cols = (Lp / 128) * Np;
+      while (pl.tcols < cols) pl.tcols *= 2;
+      if (Np > 256) pl.ok = false;
+    }
+  }
+  if (pl.tcols > 512) pl.ok = false;
+  pl.cap = tc::rup(pl.cap, 256);
+  pl.bsz = tc::rup(pl.bsz, 256);
+  pl.smem = (size_t)(2 * pl.cap + 6 * pl.bsz) * esz + 1024;
+  // keep at most 512 / tcols CTAs per SM so tensor-memory allocation never waits long
+  const size_t per_sm = 228 * 1024;
+  const size_t floor_smem = per_sm * (size_t)pl.tcols / 512 + 1024;
+  pl.smem = std::max(pl.smem, floor_smem);
+  if (pl.smem > (size_t)g_tc_dyn_max) pl.ok = false;
+  return pl;
+}
+
+// dynamic shared memory the tensor-core kernels may request: the opt-in
+// limit minus their static shared memory
+afi_status fd_tc_prepare(afi_ctx *c) {
+  cudaFuncAttributes fa2, fa1;
+  AFI_CUDA(cudaFuncGetAttributes(&fa2, k_fd_tc<2>));
+  AFI_CUDA(cudaFuncGetAttributes(&fa1, k_fd_tc<1>));
+  const int stat = (int)std::max(fa2.sharedSizeBytes, fa1.sharedSizeBytes);
+  g_tc_dyn_max = c->smem_optin - stat;
+  AFI_CUDA(cudaFuncSetAttribute(k_fd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_tc_dyn_max));
+  AFI_CUDA(cudaFuncSetAttribute(k_fd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_tc_dyn_max));
+  return AFI_OK;
+}
+
+// Tensor-core FD; returns AFI_EINVAL (without launching) if a patch does not fit.
+afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st) {
+  const int fmt = (c->opt.prec == AFI_FD_BF16) ? 1 : 2;
+  const TcPlan pl = tc_plan(c, interior, fmt);
+  if (!pl.ok) return AFI_EINVAL;
+  if (fmt == 2)
+    launch(k_fd_tc<2>, dim3(c->npatch, c->dim), 256, pl.smem, st, (const DevPatch *)c->patches,
+           (const Tab1D *)c->tabs, (const float *)c->fpool, c->dim, interior, r, s, pl.cap, pl.bsz,
+           pl.tcols, c->gate, c->dflag + 1);
+  else
+    launch(k_fd_tc<1>, dim3(c->npatch, c->dim), 256, pl.smem, st, (const DevPatch *)c->patches,
+           (const Tab1D *)c->tabs, (const float *)c->fpool, c->dim, interior, r, s, pl.cap, pl.bsz,
+           pl.tcols, c->gate, c->dflag + 1);
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
+}
+
+}  // namespace afi

@@ -348,6 +348,39 @@ __global__ void k_geneig(Tab1D *tabs, int ntab, double *pool, int interior, int 
   if (threadIdx.x == 0 && bad) atomicExch(flag, 1);
 }
 
+// Zero-padded copies U[i][a] -> Up[i*ld + a] and Upt[a*ld + i] (and the
+// interior pencil), so that mode products can load 4 coefficients at once.
+__global__ void k_pad_u(Tab1D *tabs, int ntab, double *pool) {
+  const int t = blockIdx.y;
+  if (t >= ntab) return;
+  const Tab1D T = tabs[t];
+  for (int part = 0; part < 2; ++part) {
+    const int n = part ? T.ni : T.n, ld = part ? T.ldi : T.ld;
+    const double *U = pool + (part ? T.Ui : T.U);
+    double *Up = pool + (part ? T.Uip : T.Up), *Upt = pool + (part ? T.Uipt : T.Upt);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * ld; idx += gridDim.x * blockDim.x) {
+      const int i = idx / ld, a = idx % ld;
+      Up[idx] = (a < n) ? U[i * n + a] : 0.0;
+      Upt[idx] = (a < n) ? U[a * n + i] : 0.0;
+    }
+  }
+}
+
+// Diagonal-major band copies of K_hat and M_hat (half-bandwidth p), so that
+// neighbouring output indices read neighbouring addresses.
+__global__ void k_band(Tab1D *tabs, int ntab, double *pool) {
+  const int t = blockIdx.y;
+  if (t >= ntab) return;
+  const Tab1D T = tabs[t];
+  const int W = 2 * T.p + 1;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < W * T.n; idx += gridDim.x * blockDim.x) {
+    const int tt = idx / T.n, i = idx % T.n, j = i + tt - T.p;
+    const bool in = j >= 0 && j < T.n;
+    pool[T.Kb + idx] = in ? pool[T.K + (long long)i * T.n + j] : 0.0;
+    pool[T.Mb + idx] = in ? pool[T.M + (long long)i * T.n + j] : 0.0;
+  }
+}
+
 __global__ void k_to_low(const double *src, float *f, __nv_bfloat16 *b, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -453,6 +486,8 @@ afi_status build_1d_tables(afi_ctx *c) {
   int h = 0;
   AFI_CUDA(cudaMemcpy(&h, c->dflag, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) { set_error("univariate mass pencil not positive definite"); return AFI_ESINGULAR; }
+  launch(k_pad_u, dim3(16, nt), 256, 0, 0, c->tabs, nt, c->dpool);
+  launch(k_band, dim3(16, nt), 256, 0, 0, c->tabs, nt, c->dpool);
   // low-precision copies of the eigenvectors: the pools mirror the FP64 pool
   launch(k_to_low, (unsigned)((c->dpool_n + 255) / 256), 256, 0, 0, c->dpool, c->fpool, c->bpool, c->dpool_n);
   AFI_LAUNCH_CHECK();

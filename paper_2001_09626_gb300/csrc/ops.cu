@@ -53,21 +53,29 @@ __device__ __forceinline__ void block_sum_multi(double *vals, int nv, double *sh
 }
 
 // ------------------------------------------------------- stiffness matvec
-template <int DIM>
+// One thread per node: y_l(node) = sum_m sum_o A[l][m][o][node] x_m(node + o).
+// Stencil planes have rows padded to even length n1p (padding coefficients
+// are zero); x and y use the torn layout.  Consecutive threads read
+// consecutive coefficients of one plane (coalesced).
+// PC > 0: degree known at compile time (fully unrolled neighbour rows);
+// PC = 0: any degree.
+template <int DIM, int PC>
 __global__ void __launch_bounds__(128) k_stencil_mv(const DevPatch *P, const double *__restrict__ A,
                                                     const double *__restrict__ x,
-                                                    double *__restrict__ y) {
+                                                    double *__restrict__ y, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   const DevPatch pt = P[blockIdx.y];
   const int node = blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= pt.N) return;
-  const int n1 = pt.n[0], n2 = pt.n[1], n3 = pt.n[2], p = pt.p;
+  const int n1 = pt.n[0], n2 = pt.n[1], n3 = pt.n[2], p = PC > 0 ? PC : pt.p;
   const int i1 = node % n1, i2 = (node / n1) % n2, i3 = node / (n1 * n2);
-  const int W1 = pt.W[0], W2 = pt.W[1], W3 = pt.W[2];
+  const int W1 = PC > 0 ? 2 * PC + 1 : pt.W[0], W2 = PC > 0 ? 2 * PC + 1 : pt.W[1];
+  const int W3 = (DIM == 3) ? W2 : 1;
   double acc[DIM];
 #pragma unroll
   for (int l = 0; l < DIM; ++l) acc[l] = 0.0;
-  const long long N = pt.N, S = pt.S;
-  const double *Ab = A + pt.soff + node;
+  const long long N = pt.N, S = pt.S, NP = pt.NP;
+  const double *Ab = A + pt.soff + i1 + (long long)pt.n1p * (i2 + (long long)n2 * i3);
   for (int m = 0; m < DIM; ++m) {
     const double *xm = x + pt.off + m * N;
     for (int o3 = 0; o3 < W3; ++o3) {
@@ -78,12 +86,13 @@ __global__ void __launch_bounds__(128) k_stencil_mv(const DevPatch *P, const dou
         if (j2 < 0 || j2 >= n2) continue;
         const int orow = W1 * (o2 + W2 * o3);
         const long long jrow = (long long)n1 * (j2 + (long long)n2 * j3);
+#pragma unroll
         for (int o1 = 0; o1 < W1; ++o1) {
           const int j1 = i1 + o1 - p;
           const double xv = (j1 >= 0 && j1 < n1) ? xm[jrow + j1] : 0.0;
           const long long o = orow + o1;
 #pragma unroll
-          for (int l = 0; l < DIM; ++l) acc[l] += Ab[((long long)(l * DIM + m) * S + o) * N] * xv;
+          for (int l = 0; l < DIM; ++l) acc[l] += Ab[((long long)(l * DIM + m) * S + o) * NP] * xv;
         }
       }
     }
@@ -93,8 +102,30 @@ __global__ void __launch_bounds__(128) k_stencil_mv(const DevPatch *P, const dou
 
 afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   dim3 g((c->max_N + 127) / 128, c->npatch);
-  if (c->dim == 3) launch(k_stencil_mv<3>, g, 128, 0, s, c->patches, c->stencil, x, y);
-  else launch(k_stencil_mv<2>, g, 128, 0, s, c->patches, c->stencil, x, y);
+  int pu = c->hp[0].p;   // one degree for every patch -> specialised kernel
+  for (auto &p : c->hp)
+    if (p.p != pu) pu = 0;
+  const double *A = c->stencil;
+  const DevPatch *P = c->patches;
+#define AFI_MV(D, PC) launch(k_stencil_mv<D, PC>, g, 128, 0, s, P, A, x, y, c->gate)
+  if (c->dim == 3) {
+    switch (pu) {
+      case 1: AFI_MV(3, 1); break;
+      case 2: AFI_MV(3, 2); break;
+      case 3: AFI_MV(3, 3); break;
+      case 4: AFI_MV(3, 4); break;
+      case 5: AFI_MV(3, 5); break;
+      default: AFI_MV(3, 0);
+    }
+  } else {
+    switch (pu) {
+      case 1: AFI_MV(2, 1); break;
+      case 2: AFI_MV(2, 2); break;
+      case 3: AFI_MV(2, 3); break;
+      default: AFI_MV(2, 0);
+    }
+  }
+#undef AFI_MV
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -162,17 +193,39 @@ afi_status op_BBt_inv(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
 }
 
 // ------------------------------------------------------ rigid-mode algebra
-// g[k][a] = sum over the rows touching patch k of (+-x_row) R_k(copy)[a],
-// i.e. (G^T x) restricted to patch k.
+// The rigid modes of a component-`comp` dof at point X: the translation
+// `comp` (value 1) and two rotations (3D) or one (2D), see rigid().
+struct RigidNZ { int m1, m2; double v1, v2; };
+__device__ __forceinline__ RigidNZ rigid_nz(int comp, const double *X, int dim) {
+  RigidNZ r;
+  if (dim == 2) {
+    r.m1 = 2; r.v1 = (comp == 0) ? X[1] : -X[0];
+    r.m2 = 2; r.v2 = 0.0;
+  } else if (comp == 0) {
+    r.m1 = 4; r.v1 = X[2]; r.m2 = 5; r.v2 = X[1];
+  } else if (comp == 1) {
+    r.m1 = 3; r.v1 = X[2]; r.m2 = 5; r.v2 = -X[0];
+  } else {
+    r.m1 = 3; r.v1 = -X[1]; r.m2 = 4; r.v2 = -X[0];
+  }
+  return r;
+}
+
+constexpr int kGtBlocks = 8;    // blocks per patch for the row-list reduction
+constexpr int kRtChunks = 16;   // blocks per (patch, component) for R^T v
+
+// Partial sums of (G^T x) over a strided part of the rows touching patch k:
+// part[(k * kGtBlocks + b) * NM + a].
 template <int NM>
-__global__ void __launch_bounds__(256) k_Gt(const DevPatch *P, const double *ctrl, const int *ptr,
-                                            const int2 *ent, const double *x, double *g, int dim) {
+__global__ void __launch_bounds__(256) k_Gt_part(const DevPatch *P, const double *ctrl,
+                                                 const int *ptr, const int2 *ent, const double *x,
+                                                 double *part, int dim) {
   __shared__ double sh[256 * NM];
-  const int k = blockIdx.x;
+  const int k = blockIdx.y, b = blockIdx.x;
   const DevPatch pt = P[k];
   double acc[NM];
   for (int a = 0; a < NM; ++a) acc[a] = 0.0;
-  for (int e = ptr[k] + threadIdx.x; e < ptr[k + 1]; e += blockDim.x) {
+  for (int e = ptr[k] + b * blockDim.x + threadIdx.x; e < ptr[k + 1]; e += gridDim.x * blockDim.x) {
     int2 en = ent[e];
     double xv = x[en.x >> 1];
     if (en.x & 1) xv = -xv;
@@ -182,53 +235,91 @@ __global__ void __launch_bounds__(256) k_Gt(const DevPatch *P, const double *ctr
   }
   block_sum_multi<256>(acc, NM, sh);
   if (threadIdx.x == 0)
-    for (int a = 0; a < NM; ++a) g[k * NM + a] = acc[a];
+    for (int a = 0; a < NM; ++a) part[((long long)k * gridDim.x + b) * NM + a] = acc[a];
 }
 
-// g[k][a] = R_k^T v over all dofs of patch k.
-template <int NM>
-__global__ void __launch_bounds__(256) k_Rt(const DevPatch *P, const double *ctrl, const double *v,
-                                            double *g, int dim) {
-  __shared__ double sh[256 * NM];
-  const int k = blockIdx.x;
-  const DevPatch pt = P[k];
-  double acc[NM];
-  for (int a = 0; a < NM; ++a) acc[a] = 0.0;
-  const long long n = (long long)dim * pt.N;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    int comp = (int)(i / pt.N), node = (int)(i - (long long)comp * pt.N);
-    const double *X = ctrl + pt.xoff + (long long)node * dim;
-    double xv = v[pt.off + i];
-    for (int a = 0; a < NM; ++a) acc[a] += xv * rigid(a, comp, X, dim);
-  }
-  block_sum_multi<256>(acc, NM, sh);
-  if (threadIdx.x == 0)
-    for (int a = 0; a < NM; ++a) g[k * NM + a] = acc[a];
-}
-
-// v[dof] -= sum_a R(dof)[a] y_k[a], with y_k = Minv_k g_k if Minv != null
-// (per-patch NM x NM matrices) or y_k = g_k otherwise.
-__global__ void k_Rsub(const DevPatch *P, const double *ctrl, const double *src, double *dst,
-                       const double *g, const double *Minv, int dim, int nm) {
-  const int k = blockIdx.y;
-  const DevPatch pt = P[k];
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= (long long)dim * pt.N) return;
-  double y[6];
+// g[k][a] = sum over the nb partial blocks (fixed order); optionally y = Minv_k g_k.
+__global__ void k_part_final(const double *part, int nb, int nm, int npatch, double *g,
+                             const double *Minv) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npatch) return;
+  double t[6];
   for (int a = 0; a < nm; ++a) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[((long long)k * nb + b) * nm + a];
+    t[a] = s;
+  }
+  for (int a = 0; a < nm; ++a) {
+    double v = t[a];
     if (Minv) {
-      double s = 0.0;
-      for (int b = 0; b < nm; ++b) s += Minv[(k * nm + a) * nm + b] * g[k * nm + b];
-      y[a] = s;
-    } else {
-      y[a] = g[k * nm + a];
+      v = 0.0;
+      for (int b = 0; b < nm; ++b) v += Minv[((long long)k * nm + a) * nm + b] * t[b];
+    }
+    g[k * nm + a] = v;
+  }
+}
+
+// Partial sums of R_k^T v over one chunk of one component block: the
+// translation and the two rotation products, part[((k*dim + comp)*CH + ch)*3].
+__global__ void __launch_bounds__(256) k_Rt_part(const DevPatch *P, const double *ctrl,
+                                                 const double *v, double *part, int dim) {
+  __shared__ double sh[256 * 3];
+  const int ch = blockIdx.x, comp = blockIdx.y, k = blockIdx.z;
+  const DevPatch pt = P[k];
+  const double *vc = v + pt.off + (long long)comp * pt.N;
+  const double *Xb = ctrl + pt.xoff;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int i = ch * blockDim.x + threadIdx.x; i < pt.N; i += gridDim.x * blockDim.x) {
+    const double xv = vc[i];
+    const RigidNZ r = rigid_nz(comp, Xb + (long long)i * dim, dim);
+    acc[0] += xv;
+    acc[1] += xv * r.v1;
+    acc[2] += xv * r.v2;
+  }
+  block_sum_multi<256>(acc, 3, sh);
+  if (threadIdx.x == 0)
+    for (int a = 0; a < 3; ++a) part[(((long long)k * dim + comp) * gridDim.x + ch) * 3 + a] = acc[a];
+}
+
+// g[k][a] from the R^T v partials (fixed order), optionally y = Minv_k g_k.
+__global__ void k_Rt_final(const double *part, int nch, int dim, int nm, int npatch, double *g,
+                           const double *Minv) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npatch) return;
+  double t[6] = {0, 0, 0, 0, 0, 0};
+  const double X0[3] = {0.0, 0.0, 0.0};
+  for (int comp = 0; comp < dim; ++comp) {
+    const RigidNZ r = rigid_nz(comp, X0, dim);   // only the mode indices are used
+    for (int ch = 0; ch < nch; ++ch) {
+      const double *q = part + (((long long)k * dim + comp) * nch + ch) * 3;
+      t[comp] += q[0];
+      t[r.m1] += q[1];
+      if (dim == 3) t[r.m2] += q[2];
     }
   }
-  int comp = (int)(i / pt.N), node = (int)(i - (long long)comp * pt.N);
-  const double *X = ctrl + pt.xoff + (long long)node * dim;
-  double s = 0.0;
-  for (int a = 0; a < nm; ++a) s += rigid(a, comp, X, dim) * y[a];
-  dst[pt.off + i] = src[pt.off + i] - s;
+  for (int a = 0; a < nm; ++a) {
+    double v = t[a];
+    if (Minv) {
+      v = 0.0;
+      for (int b = 0; b < nm; ++b) v += Minv[((long long)k * nm + a) * nm + b] * t[b];
+    }
+    g[k * nm + a] = v;
+  }
+}
+
+// dst = src - R_k y_k on every dof (y per patch, NM entries).
+__global__ void k_Rsub(const DevPatch *P, const double *ctrl, const double *src, double *dst,
+                       const double *y, int dim, int nm) {
+  const int comp = blockIdx.y, k = blockIdx.z;
+  const DevPatch pt = P[k];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= pt.N) return;
+  const RigidNZ r = rigid_nz(comp, ctrl + pt.xoff + (long long)i * dim, dim);
+  const double *yk = y + k * nm;
+  double sub = yk[comp] + r.v1 * yk[r.m1];
+  if (dim == 3) sub += r.v2 * yk[r.m2];
+  const long long at = pt.off + (long long)comp * pt.N + i;
+  dst[at] = src[at] - sub;
 }
 
 // dense y = M g (M: n x n), one warp per row.
@@ -264,17 +355,26 @@ __global__ void k_G(const DevPatch *P, const double *ctrl, const int2 *rc, const
 }
 
 afi_status op_Gt_rows(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
-  if (c->nm == 6) launch(k_Gt<6>, c->npatch, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, g, c->dim);
-  else launch(k_Gt<3>, c->npatch, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, g, c->dim);
+  dim3 gr(kGtBlocks, c->npatch);
+  if (c->nm == 6) launch(k_Gt_part<6>, gr, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, c->part, c->dim);
+  else launch(k_Gt_part<3>, gr, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, c->part, c->dim);
+  launch(k_part_final, (c->npatch + 127) / 128, 128, 0, s, (const double *)c->part, kGtBlocks, c->nm,
+         c->npatch, g, (const double *)nullptr);
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
+}
+
+// g = R^T v per patch; with Minv, g = Minv_k (R_k^T v) instead.
+static afi_status Rt_apply(afi_ctx *c, const double *x, double *g, const double *Minv, cudaStream_t s) {
+  launch(k_Rt_part, dim3(kRtChunks, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x, c->part, c->dim);
+  launch(k_Rt_final, (c->npatch + 127) / 128, 128, 0, s, (const double *)c->part, kRtChunks, c->dim,
+         c->nm, c->npatch, g, Minv);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 afi_status op_Rt(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
-  if (c->nm == 6) launch(k_Rt<6>, c->npatch, 256, 0, s, c->patches, c->ctrl, x, g, c->dim);
-  else launch(k_Rt<3>, c->npatch, 256, 0, s, c->patches, c->ctrl, x, g, c->dim);
-  AFI_LAUNCH_CHECK();
-  return AFI_OK;
+  return Rt_apply(c, x, g, nullptr, s);
 }
 
 afi_status op_dense_inv(afi_ctx *c, const double *g, double *y, cudaStream_t s) {
@@ -309,17 +409,18 @@ afi_status op_G(afi_ctx *c, const double *y, double *out, bool subtract, cudaStr
 }
 
 afi_status op_Pu(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
+  // P_u x = x - R (R^T R)^{-1} R^T x, patch by patch
   double *g = gbuf(c, 0);
-  AFI_TRY(op_Rt(c, x, g, s));
-  dim3 gr((unsigned)((c->dim * c->max_N + 255) / 256), c->npatch);
-  launch(k_Rsub, gr, 256, 0, s, c->patches, c->ctrl, x, y, g, c->RtR_inv, c->dim, c->nm);
+  AFI_TRY(Rt_apply(c, x, g, c->RtR_inv, s));
+  launch(k_Rsub, dim3((c->max_N + 255) / 256, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x,
+         y, (const double *)g, c->dim, c->nm);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 afi_status op_R_sub(afi_ctx *c, const double *y, double *v, cudaStream_t s) {
-  dim3 gr((unsigned)((c->dim * c->max_N + 255) / 256), c->npatch);
-  launch(k_Rsub, gr, 256, 0, s, c->patches, c->ctrl, v, v, y, nullptr, c->dim, c->nm);
+  launch(k_Rsub, dim3((c->max_N + 255) / 256, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl,
+         (const double *)v, v, y, c->dim, c->nm);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -403,10 +504,18 @@ afi_status op_saddle(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
 }
 
 // -------------------------------------------------------------- MINRES
+// Scalars of the recurrences live on the device (c->small); every kernel of
+// one iteration reads S_ACTIVE, set by k_iter_begin, so that iterations after
+// convergence (inside a replayed graph) leave the state untouched.
 enum { S_BETA1 = 0, S_BETA, S_OLDB, S_ALFA, S_DBAR, S_EPSLN, S_OLDEPS, S_PHIBAR, S_CS, S_SN,
-       S_DELTA, S_GAMMA, S_PHI, S_REL, S_BETA2, S_FLAG, S_DOT, S_BNORM2, S_RES2, S_COUNT };
+       S_DELTA, S_GAMMA, S_PHI, S_REL, S_BETA2, S_FLAG, S_DOT, S_BNORM2, S_RES2, S_INVBETA,
+       S_BOVERO, S_INVGAMMA, S_ACTIVE, S_ITN, S_NEXTCHECK, S_MAXIT, S_COUNT };
 
-__global__ void k_minres_init(double *st) {
+constexpr int kRelHist = 64;   // st[64 + itn % 8]: estimate of the last 8 iterations
+constexpr int kHostStats = kRelHist + 8;
+
+__global__ void k_minres_init(double *st, double maxit) {
+  for (int i = 0; i < 8; ++i) st[kRelHist + i] = 1.0;
   double b2 = st[S_BETA2];
   double beta1 = (b2 >= 0.0 && isfinite(b2)) ? sqrt(b2) : -1.0;
   st[S_BETA1] = beta1;
@@ -418,27 +527,32 @@ __global__ void k_minres_init(double *st) {
   st[S_CS] = -1.0;
   st[S_SN] = 0.0;
   st[S_REL] = 1.0;
+  st[S_INVBETA] = (beta1 > 0.0) ? 1.0 / beta1 : 0.0;
+  st[S_BOVERO] = 0.0;   // the first iteration has no r1 term
+  st[S_ACTIVE] = 0.0;
+  st[S_ITN] = 0.0;
+  st[S_NEXTCHECK] = 0.0;
+  st[S_MAXIT] = maxit;
   st[S_FLAG] = (beta1 < 0.0) ? 2.0 : (beta1 == 0.0 ? 1.0 : 0.0);
 }
 
-__global__ void k_v_from_y(const double *y, double *v, long n, const double *st) {
-  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  v[i] = y[i] / st[S_BETA];
+__global__ void k_iter_begin(double *st) {
+  const bool act = st[S_FLAG] == 0.0 && st[S_ITN] < st[S_MAXIT];
+  st[S_ACTIVE] = act ? 1.0 : 0.0;
+  if (act) st[S_ITN] += 1.0;
 }
 
-// y -= (beta/oldb) r1 (unless first), partial dots of v.y
-__global__ void k_y_upd1(double *y, const double *r1, const double *v, long n, const double *st,
-                         int first, double *part) {
+__global__ void k_set(double *st, int idx, double v) { st[idx] = v; }
+
+__global__ void k_v_from_y(const double *y, double *v, long n, const double *st) {
+  if (st[S_ACTIVE] == 0.0) return;
+  long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  v[i] = y[i] * st[S_INVBETA];
+}
+
+__device__ __forceinline__ void block_partial(double s, double *part) {
   __shared__ double sh[256];
-  double coef = first ? 0.0 : st[S_BETA] / st[S_OLDB];
-  double s = 0.0;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    double yi = y[i];
-    if (!first) yi -= coef * r1[i];
-    y[i] = yi;
-    s += v[i] * yi;
-  }
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {
@@ -448,20 +562,66 @@ __global__ void k_y_upd1(double *y, const double *r1, const double *v, long n, c
   if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
+// y = A v - (beta/oldb) r1 (A v given in av), partial dots of v.y
+__global__ void k_y_upd1(const double *av, double *y, const double *r1, const double *v, long n,
+                         const double *st, double *part) {
+  if (st[S_ACTIVE] == 0.0) return;
+  const double coef = st[S_BOVERO];
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double yi = av[i] - coef * r1[i];
+    y[i] = yi;
+    s += v[i] * yi;
+  }
+  block_partial(s, part);
+}
+
 __global__ void k_y_upd2(double *y, const double *r2, long n, const double *st) {
+  if (st[S_ACTIVE] == 0.0) return;
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  y[i] -= (st[S_ALFA] / st[S_BETA]) * r2[i];
+  y[i] -= (st[S_ALFA] * st[S_INVBETA]) * r2[i];
+}
+
+// y = M^{-1} r2 (given in mr) and partial dots of r2.y
+__global__ void k_dot_copy(const double *r2, const double *mr, double *y, long n, const double *st,
+                           double *part) {
+  if (st[S_ACTIVE] == 0.0) return;
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double yi = mr[i];
+    y[i] = yi;
+    s += r2[i] * yi;
+  }
+  block_partial(s, part);
+}
+
+__global__ void k_sum_active(const double *part, int nb, double *st, int slot) {
+  if (st[S_ACTIVE] == 0.0) return;
+  __shared__ double sh[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st[slot] = sh[0];
 }
 
 __global__ void k_minres_scalars(double *st, double tol) {
+  if (st[S_ACTIVE] == 0.0) return;
   double beta2 = st[S_BETA2];
   if (!(beta2 >= 0.0) || !isfinite(beta2)) { st[S_FLAG] = 2.0; return; }
   double beta = st[S_BETA], alfa = st[S_ALFA];
   double cs = st[S_CS], sn = st[S_SN], dbar = st[S_DBAR], phibar = st[S_PHIBAR];
   st[S_OLDB] = beta;
+  const double oldb = beta;
   beta = sqrt(beta2);
   st[S_BETA] = beta;
+  st[S_INVBETA] = 1.0 / beta;
+  st[S_BOVERO] = beta / oldb;
   st[S_OLDEPS] = st[S_EPSLN];
   double delta = cs * dbar + sn * alfa;
   double gbar = sn * dbar - cs * alfa;
@@ -475,21 +635,24 @@ __global__ void k_minres_scalars(double *st, double tol) {
   phibar = sn * phibar;
   st[S_DELTA] = delta;
   st[S_GAMMA] = gamma;
+  st[S_INVGAMMA] = 1.0 / gamma;
   st[S_CS] = cs;
   st[S_SN] = sn;
   st[S_PHI] = phi;
   st[S_PHIBAR] = phibar;
   double rel = phibar / st[S_BETA1];
   st[S_REL] = rel;
+  st[kRelHist + ((long)st[S_ITN] % 8)] = rel;
   if (!isfinite(rel)) st[S_FLAG] = 2.0;
-  else if (rel <= tol) st[S_FLAG] = 1.0;
+  else if (rel <= tol && st[S_ITN] >= st[S_NEXTCHECK]) st[S_FLAG] = 1.0;
 }
 
 __global__ void k_w_upd(const double *v, const double *w1, const double *w2, double *wn, double *x,
                         long n, const double *st) {
+  if (st[S_ACTIVE] == 0.0) return;
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double w = (v[i] - st[S_OLDEPS] * w1[i] - st[S_DELTA] * w2[i]) / st[S_GAMMA];
+  double w = (v[i] - st[S_OLDEPS] * w1[i] - st[S_DELTA] * w2[i]) * st[S_INVGAMMA];
   wn[i] = w;
   x[i] += st[S_PHI] * w;
 }
@@ -508,115 +671,200 @@ __global__ void k_add(const double *a, const double *b, double *out, long n) {
 
 static inline unsigned nblk(long n) { return (unsigned)((n + 255) / 256); }
 
+// Buffers of the iteration: three rotating Krylov vectors B (r1, r2, y), two
+// rotating search directions W, and fixed v, x and operator outputs tA, tB.
+struct MinresBufs { double *b, *x, *v, *B[3], *W[2], *tA, *tB, *tmp, *lam0; };
+
+static MinresBufs minres_bufs(afi_ctx *c) {
+  const long nt = c->n_dof + c->n_c;
+  double *V = c->ws + kOpScratch * nt;
+  MinresBufs M;
+  M.b = V; M.x = V + nt; M.v = V + 2 * nt;
+  M.B[0] = V + 3 * nt; M.B[1] = V + 4 * nt; M.B[2] = V + 5 * nt;
+  M.W[0] = V + 6 * nt; M.W[1] = V + 7 * nt;
+  M.tA = V + 8 * nt; M.tB = V + 9 * nt; M.tmp = V + 10 * nt; M.lam0 = V + 11 * nt;
+  return M;
+}
+
+// Enqueue one MINRES iteration after t completed ones (roles rotate with t).
+static afi_status enqueue_iteration(afi_ctx *c, const MinresBufs &M, long t, cudaStream_t s) {
+  const long nt = c->n_dof + c->n_c;
+  double *st = c->small;
+  double *r1 = M.B[t % 3], *r2 = M.B[(t + 1) % 3], *y = M.B[(t + 2) % 3];
+  double *w1 = M.W[t % 2], *w2 = M.W[(t + 1) % 2];
+  launch(k_iter_begin, 1, 1, 0, s, st);
+  launch(k_v_from_y, nblk(nt), 256, 0, s, (const double *)y, M.v, nt, (const double *)st);
+  // the heavy operator kernels skip their work in inactive iterations
+  struct GateScope {
+    afi_ctx *c;
+    GateScope(afi_ctx *cc, const double *g) : c(cc) { c->gate = g; }
+    ~GateScope() { c->gate = nullptr; }
+  } gate_scope(c, st + S_ACTIVE);
+  AFI_TRY(op_saddle(c, M.v, M.tA, s));
+  launch(k_y_upd1, kDotBlocks, 256, 0, s, (const double *)M.tA, y, (const double *)r1,
+         (const double *)M.v, nt, (const double *)st, c->small + kPart);
+  launch(k_sum_active, 1, 1024, 0, s, (const double *)(c->small + kPart), kDotBlocks, st, (int)S_ALFA);
+  launch(k_y_upd2, nblk(nt), 256, 0, s, y, (const double *)r2, nt, (const double *)st);
+  // roles now: r1' = r2, r2' = y, y' = r1
+  AFI_TRY(op_precond(c, y, M.tB, s));
+  launch(k_dot_copy, kDotBlocks, 256, 0, s, (const double *)y, (const double *)M.tB, r1, nt,
+         (const double *)st, c->small + kPart);
+  launch(k_sum_active, 1, 1024, 0, s, (const double *)(c->small + kPart), kDotBlocks, st, (int)S_BETA2);
+  launch(k_minres_scalars, 1, 1, 0, s, st, c->opt.tol);
+  launch(k_w_upd, nblk(nt), 256, 0, s, (const double *)M.v, (const double *)w1, (const double *)w2,
+         w1, M.x, nt, (const double *)st);
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
+}
+
+constexpr int kGraphIters = 6;   // lcm of the rotation periods 3 and 2
+
+// Capture kGraphIters iterations on the context's private stream (the caller's
+// stream may be the legacy default stream, which cannot be captured); the
+// graph is then launched on the caller's stream.
+static afi_status ensure_graph(afi_ctx *c, const MinresBufs &M) {
+  if (c->graph_exec && c->graph_prec == (int)c->opt.prec) return AFI_OK;
+  cudaStream_t s = (cudaStream_t)c->cap_stream;
+  if (c->graph_exec) { cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec); c->graph_exec = nullptr; }
+  cudaGraph_t g = nullptr;
+  const long long before = g_launches.load();
+  AFI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  afi_status st = AFI_OK;
+  for (int i = 0; i < kGraphIters && st == AFI_OK; ++i) st = enqueue_iteration(c, M, i, s);
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  g_launches.fetch_sub(g_launches.load() - before);
+  if (st != AFI_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(e)); return AFI_ECUDA; }
+  size_t nodes = 0;
+  cudaGraphGetNodes(g, nullptr, &nodes);
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(e)); return AFI_ECUDA; }
+  c->graph_exec = ex;
+  c->graph_nodes = (long long)nodes;
+  c->graph_prec = (int)c->opt.prec;
+  return AFI_OK;
+}
+
 // one right-hand side
 afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, afi_info *info,
                      cudaStream_t s) {
   const long n = c->n_dof, m = c->n_c, nt = n + m;
-  double *V = c->ws + kOpScratch * (n + m);   // Krylov vectors after the operator scratch
-  double *b = V, *x = V + nt, *v = V + 2 * nt;
-  double *buf[3] = {V + 3 * nt, V + 4 * nt, V + 5 * nt};   // r1, r2, y rotation
-  double *wb[2] = {V + 6 * nt, V + 7 * nt};                 // older / newer w
-  double *tmp = V + 9 * nt, *lam0 = V + 10 * nt;
+  const MinresBufs M = minres_bufs(c);
   double *st = c->small;
   cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  cudaEventRecord(e0, s);
+  AFI_CUDA(cudaEventCreate(&e0));
+  AFI_CUDA(cudaEventCreate(&e1));
+  AFI_CUDA(cudaEventRecord(e0, s));
   // lambda_0 = G (G^T G)^{-1} R^T f and b = [f - B^T lambda_0; 0]
   if (m > 0) {
     AFI_TRY(op_Rt(c, f, gbuf(c, 0), s));
     AFI_TRY(op_dense_inv(c, gbuf(c, 0), gbuf(c, 1), s));
-    AFI_TRY(G_apply(c, gbuf(c, 1), lam0, nullptr, s));
+    AFI_TRY(G_apply(c, gbuf(c, 1), M.lam0, nullptr, s));
   }
-  AFI_CUDA(cudaMemcpyAsync(b, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AFI_CUDA(cudaMemcpyAsync(M.b, f, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (m > 0) {
-    AFI_TRY(op_Bt_scaled(c, lam0, b, -1.0, true, false, s));
-    AFI_CUDA(cudaMemsetAsync(b + n, 0, m * sizeof(double), s));
+    AFI_TRY(op_Bt_scaled(c, M.lam0, M.b, -1.0, true, false, s));
+    AFI_CUDA(cudaMemsetAsync(M.b + n, 0, m * sizeof(double), s));
   }
-  AFI_CUDA(cudaMemsetAsync(x, 0, nt * sizeof(double), s));
-  AFI_CUDA(cudaMemsetAsync(wb[0], 0, nt * sizeof(double), s));
-  AFI_CUDA(cudaMemsetAsync(wb[1], 0, nt * sizeof(double), s));
-  double *r1 = buf[0], *r2 = buf[1], *y = buf[2];
-  AFI_CUDA(cudaMemcpyAsync(r1, b, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  AFI_CUDA(cudaMemcpyAsync(r2, b, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  AFI_TRY(op_precond(c, r1, y, s));
-  AFI_TRY(dot(c, r1, y, nt, st + S_BETA2, s));
-  AFI_TRY(dot(c, b, b, nt, st + S_BNORM2, s));
-  launch(k_minres_init, 1, 1, 0, s, st);
+  AFI_CUDA(cudaMemsetAsync(M.x, 0, nt * sizeof(double), s));
+  AFI_CUDA(cudaMemsetAsync(M.W[0], 0, nt * sizeof(double), s));
+  AFI_CUDA(cudaMemsetAsync(M.W[1], 0, nt * sizeof(double), s));
+  // r1 = r2 = b, y = M^{-1} b
+  AFI_CUDA(cudaMemcpyAsync(M.B[0], M.b, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AFI_CUDA(cudaMemcpyAsync(M.B[1], M.b, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AFI_TRY(op_precond(c, M.B[0], M.B[2], s));
+  AFI_TRY(dot(c, M.B[0], M.B[2], nt, st + S_BETA2, s));
+  AFI_TRY(dot(c, M.b, M.b, nt, st + S_BNORM2, s));
+  launch(k_minres_init, 1, 1, 0, s, st, (double)c->opt.maxit);
   AFI_LAUNCH_CHECK();
+  const bool use_graph = c->opt.use_graph != 0;
+  if (use_graph) AFI_TRY(ensure_graph(c, M));
   double *hs = c->host_small;
-  AFI_CUDA(cudaMemcpyAsync(hs, st, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
   AFI_CUDA(cudaStreamSynchronize(s));
-  int itn = 0;
   afi_status status = AFI_OK;
   const double tol = c->opt.tol;
   const double bnorm = sqrt(hs[S_BNORM2]);
   double relres_true = 0.0;
-  int last_check = -1000000;
+  long t = 0;            // completed iterations (buffer roles)
+  long checked_at = -1;  // iteration of the last true-residual check
   if (hs[S_FLAG] == 2.0) status = AFI_EBREAKDOWN;
   bool done = (hs[S_FLAG] != 0.0);
-  double *w1 = wb[0], *w2 = wb[1];
-  while (!done && itn < c->opt.maxit) {
-    ++itn;
-    launch(k_v_from_y, nblk(nt), 256, 0, s, y, v, nt, st);
-    AFI_TRY(op_saddle(c, v, y, s));
-    launch(k_y_upd1, kDotBlocks, 256, 0, s, y, r1, v, nt, st, itn == 1, c->small + kPart);
-    launch(k_sum_final, 1, 1024, 0, s, c->small + kPart, kDotBlocks, st + S_ALFA);
-    launch(k_y_upd2, nblk(nt), 256, 0, s, y, r2, nt, st);
-    AFI_LAUNCH_CHECK();
-    double *t = r1; r1 = r2; r2 = y; y = t;
-    AFI_TRY(op_precond(c, r2, y, s));
-    AFI_TRY(dot(c, r2, y, nt, st + S_BETA2, s));
-    launch(k_minres_scalars, 1, 1, 0, s, st, tol);
-    // w update uses the rotated buffers: new w overwrites w1's storage
-    launch(k_w_upd, nblk(nt), 256, 0, s, v, w1, w2, w1, x, nt, st);
-    AFI_LAUNCH_CHECK();
-    double *tw = w1; w1 = w2; w2 = tw;   // (w1, w2) <- (old w2, new w)
-    AFI_CUDA(cudaMemcpyAsync(hs, st, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  while (!done && status == AFI_OK) {
+    if (use_graph && t % kGraphIters == 0) {
+      AFI_CUDA(cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, s));
+      g_launches.fetch_add(c->graph_nodes);
+      t += kGraphIters;
+    } else {
+      AFI_TRY(enqueue_iteration(c, M, t, s));
+      t += 1;
+    }
+    AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFI_CUDA(cudaStreamSynchronize(s));
+    const long itn = (long)hs[S_ITN];
     if (hs[S_FLAG] == 2.0) { status = AFI_EBREAKDOWN; break; }
-    if (hs[S_FLAG] == 1.0 && itn - last_check >= 5) {
-      last_check = itn;
-      AFI_TRY(op_saddle(c, x, tmp, s));
-      launch(k_sub, nblk(nt), 256, 0, s, b, tmp, tmp, nt);
-      AFI_TRY(dot(c, tmp, tmp, nt, st + S_RES2, s));
-      AFI_CUDA(cudaMemcpyAsync(hs, st, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (hs[S_FLAG] == 1.0) {
+      // estimate converged at iteration itn: confirm with the true residual
+      AFI_TRY(op_saddle(c, M.x, M.tmp, s));
+      launch(k_sub, nblk(nt), 256, 0, s, (const double *)M.b, (const double *)M.tmp, M.tmp, nt);
+      AFI_TRY(dot(c, M.tmp, M.tmp, nt, st + S_RES2, s));
+      AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
       AFI_CUDA(cudaStreamSynchronize(s));
       relres_true = sqrt(hs[S_RES2]) / (bnorm > 0 ? bnorm : 1.0);
-      if (relres_true <= tol) done = true;
+      checked_at = itn;
+      if (relres_true <= tol) { done = true; break; }
+      // continue from iteration itn; next check where the estimate's recent
+      // reduction rate would bring the true residual to tol (5..50 later)
+      long extra = 5;
+      if (itn >= 5) {
+        const double rn = hs[kRelHist + itn % 8], r5 = hs[kRelHist + (itn - 5) % 8];
+        if (rn > 0.0 && r5 > 0.0) {
+          const double q = pow(rn / r5, 0.2);
+          if (q > 0.0 && q < 1.0) extra = (long)ceil(log(relres_true / tol) / (-log(q)));
+        }
+      }
+      extra = std::min(std::max(extra, 5L), 50L);
+      launch(k_set, 1, 1, 0, s, st, (int)S_NEXTCHECK, (double)(itn + extra));
+      launch(k_set, 1, 1, 0, s, st, (int)S_FLAG, 0.0);
+      AFI_LAUNCH_CHECK();
     }
+    t = itn;   // the data state corresponds to the executed iterations
+    if (itn >= c->opt.maxit) { status = AFI_ENOT_CONVERGED; break; }
   }
-  if (!done && status == AFI_OK) status = AFI_ENOT_CONVERGED;
-  // true residual of the final iterate if not just measured
-  if (last_check != itn) {
-    AFI_TRY(op_saddle(c, x, tmp, s));
-    launch(k_sub, nblk(nt), 256, 0, s, b, tmp, tmp, nt);
-    AFI_TRY(dot(c, tmp, tmp, nt, st + S_RES2, s));
-    AFI_CUDA(cudaMemcpyAsync(hs, st, S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  const long itn_final = (long)hs[S_ITN];
+  if (checked_at != itn_final) {   // true residual of the final iterate
+    AFI_TRY(op_saddle(c, M.x, M.tmp, s));
+    launch(k_sub, nblk(nt), 256, 0, s, (const double *)M.b, (const double *)M.tmp, M.tmp, nt);
+    AFI_TRY(dot(c, M.tmp, M.tmp, nt, st + S_RES2, s));
+    AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
     AFI_CUDA(cudaStreamSynchronize(s));
     relres_true = sqrt(hs[S_RES2]) / (bnorm > 0 ? bnorm : 1.0);
   }
   // recovery: u = w - R (G^T G)^{-1} G^T B w, lambda = lambda_0 + chi
-  AFI_CUDA(cudaMemcpyAsync(u, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AFI_CUDA(cudaMemcpyAsync(u, M.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (m > 0) {
-    double *t = tmp;   // B w
-    AFI_TRY(op_B(c, x, t, s));
-    AFI_TRY(op_Gt_rows(c, t, gbuf(c, 0), s));
+    AFI_TRY(op_B(c, M.x, M.tmp, s));
+    AFI_TRY(op_Gt_rows(c, M.tmp, gbuf(c, 0), s));
     AFI_TRY(op_dense_inv(c, gbuf(c, 0), gbuf(c, 1), s));
     AFI_TRY(op_R_sub(c, gbuf(c, 1), u, s));
     if (lam_out) {
-      launch(k_add, nblk(m), 256, 0, s, lam0, x + n, lam_out, m);
+      launch(k_add, nblk(m), 256, 0, s, (const double *)M.lam0, (const double *)(M.x + n), lam_out, m);
       AFI_LAUNCH_CHECK();
     }
   }
-  cudaEventRecord(e1, s);
+  AFI_CUDA(cudaEventRecord(e1, s));
   AFI_CUDA(cudaEventSynchronize(e1));
+  int tc_timeout = 0;   // set by a tensor-core kernel whose bounded wait ran out
+  AFI_CUDA(cudaMemcpy(&tc_timeout, c->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (tc_timeout && status == AFI_OK) status = AFI_ETIMEOUT;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (info) {
-    info->iters = itn;
+    info->iters = (int)itn_final;
     info->relres_est = hs[S_REL];
     info->relres_true = relres_true;
     info->t_setup_ms = c->t_setup_ms;
@@ -624,6 +872,7 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   }
   if (status == AFI_EBREAKDOWN) set_error("MINRES breakdown (non-finite or negative norm)");
   if (status == AFI_ENOT_CONVERGED) set_error("MINRES reached maxit before the tolerance");
+  if (status == AFI_ETIMEOUT) set_error("a tensor-core local solve timed out waiting for its MMAs");
   return status;
 }
 

@@ -201,6 +201,11 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
       T.U = take((long long)T.n * T.n); T.D = take(T.n);
       T.Ui = take((long long)T.ni * T.ni); T.Di = take(T.ni);
     }
+    T.ld = (T.n + 3) & ~3;
+    T.ldi = (T.ni + 3) & ~3;
+    T.Up = take((long long)T.n * T.ld); T.Upt = take((long long)T.n * T.ld);
+    T.Uip = take((long long)T.ni * T.ldi); T.Uipt = take((long long)T.ni * T.ldi);
+    T.Kb = take((long long)(2 * T.p + 1) * T.n); T.Mb = take((long long)(2 * T.p + 1) * T.n);
     T.Uf = T.U; T.Uif = T.Ui; T.Ub = T.U; T.Uib = T.Ui;   // low-precision pools mirror offsets
     c->htab.push_back(T);
     return (int)c->htab.size() - 1;
@@ -244,7 +249,9 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     P.NQ = P.nq[0] * P.nq[1] * P.nq[2];
     P.off = off; off += (long long)D * P.N;
     P.ioff = ioff; ioff += (long long)D * P.Ni;
-    P.soff = soff; soff += (long long)D * D * P.S * P.N;
+    P.n1p = P.n[0] + (P.n[0] & 1);
+    P.NP = P.n1p * P.n[1] * P.n[2];
+    P.soff = soff; soff += (long long)D * D * P.S * P.NP;
     P.qoff = qoff; qoff += P.NQ;
     P.xoff = xoff; xoff += (long long)D * P.N;
     P.lam = prob->lame[2 * k];
@@ -271,6 +278,8 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   AFI_TRY(upload(c, &c->patches, c->hp));
   std::vector<double> hctrl(prob->ctrl, prob->ctrl + xoff);
   AFI_TRY(upload(c, &c->ctrl, hctrl));
+  AFI_TRY(fd_prepare(c));
+  AFI_TRY(fd_tc_prepare(c));
   AFI_TRY(build_1d_tables(c));
   launch(k_patch_H, NP, 256, 0, 0, c->patches, c->ctrl, D);
   AFI_LAUNCH_CHECK();
@@ -278,6 +287,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   AFI_TRY(dalloc(c, (void **)&c->qgeo, (size_t)(D * D + 1) * qoff * sizeof(double)));
   AFI_TRY(compute_geometry(c));
   AFI_TRY(dalloc(c, (void **)&c->stencil, (size_t)soff * sizeof(double)));
+  AFI_CUDA(cudaMemset(c->stencil, 0, (size_t)soff * sizeof(double)));   // padded nodes stay 0
   AFI_TRY(assemble_stiffness(c));
 
   // ---- connectivity: group interface control points by coordinates
@@ -456,8 +466,14 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   c->fdscratch_n = 4LL * c->n_dof + 16;
   AFI_TRY(dalloc(c, (void **)&c->fdscratch, c->fdscratch_n * sizeof(double)));
   AFI_TRY(dalloc(c, (void **)&c->small, kSmallDoubles * sizeof(double)));
+  AFI_TRY(dalloc(c, (void **)&c->part, (size_t)NP * 64 * 6 * sizeof(double)));
   AFI_CUDA(cudaMemset(c->small, 0, kSmallDoubles * sizeof(double)));
-  AFI_CUDA(cudaMallocHost((void **)&c->host_small, 64 * sizeof(double)));
+  AFI_CUDA(cudaMallocHost((void **)&c->host_small, 128 * sizeof(double)));
+  {
+    cudaStream_t cs = nullptr;
+    AFI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    c->cap_stream = cs;
+  }
   AFI_CUDA(cudaDeviceSynchronize());
   auto t1 = std::chrono::steady_clock::now();
   c->t_setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -465,10 +481,13 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
 }
 
 void free_context(afi_ctx *c) {
+  if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+  if (c->cap_stream) cudaStreamDestroy((cudaStream_t)c->cap_stream);
   void *ptrs[] = {c->patches, c->tabs, c->dpool, c->fpool, c->bpool, c->ctrl, c->stencil,
                   c->qgeo, c->row_copy, c->row_grp, c->row_patch, c->shell_dof, c->bt_ptr,
                   c->bt_ent, c->prow_ptr, c->prow_ent, c->pair_ptr, c->pair_kk, c->pair_ent,
-                  c->GtG, c->GtG_inv, c->RtR_inv, c->ws, c->fdscratch, c->small, c->dflag};
+                  c->GtG, c->GtG_inv, c->RtR_inv, c->ws, c->fdscratch, c->small, c->part,
+                  c->dflag};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);

@@ -13,14 +13,15 @@ from . import afieti as _a
 
 
 class Solver:
-    def __init__(self, problem, prec="fp64", tol=1e-8, maxit=2000, device=None):
+    def __init__(self, problem, prec="fp64", tol=1e-8, maxit=2000, device=None, use_graph=False):
         if not torch.cuda.is_available():
             raise RuntimeError("libafieti needs a CUDA device")
         self.device = torch.device(device or "cuda")
         self.problem = problem
         with torch.cuda.device(self.device):
             self._P = _a.Problem(problem)
-            self.ctx = _a.af_ieti_setup(self._P, prec=prec, tol=tol, maxit=maxit)
+            self.ctx = _a.af_ieti_setup(self._P, prec=prec, tol=tol, maxit=maxit,
+                                        use_graph=use_graph)
         self.n_dof, self.n_c = _a.afi_sizes(self.ctx)
         self.last_info = None
 

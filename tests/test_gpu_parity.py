@@ -6,8 +6,12 @@ Tolerances (FP64 paths): operators that are sums of O(10^3) products are
 compared at 1e-11 relative to the norm of the result; solves at 1e-7
 relative (tolerance 1e-10 of the iterative solve against the direct solve).
 FP32 local solvers: 2e-5 relative per application (FP32 unit roundoff times
-the O(n) accumulation length and the conditioning of U), and the converged
-solution still at 1e-7 (the preconditioner changes only the iteration)."""
+the O(n) accumulation length and the conditioning of U); TF32 (operands
+truncated to a 10-bit mantissa, error up to 9.8e-4 each) 1e-2 and BF16 (7-bit
+mantissa, 3.9e-3) 3e-2 per application, the same accumulation argument over
+six mode products.  Whatever the local-solver
+precision, the converged solution is compared at 1e-7 (the preconditioner
+changes only the iteration)."""
 import numpy as np
 import pytest
 
@@ -76,7 +80,8 @@ def test_jumps_and_projections(case):
     assert rel(s.apply(A.AFI_OP_PU, T(x)).cpu().numpy(), orc.P_u(x)) < 1e-11
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5), ("tf32", 1e-2),
+                                      ("bf16", 3e-2)])
 def test_fd_apply(case, prec, tol):
     _, prob, orc, s = case
     from paper_2001_09626_gb300 import afieti as A
@@ -89,7 +94,8 @@ def test_fd_apply(case, prec, tol):
         s.set_precision("fp64")
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5), ("tf32", 1e-2),
+                                      ("bf16", 3e-2)])
 def test_interior_fd(case, prec, tol):
     _, prob, orc, s = case
     s.set_precision(prec)
@@ -137,7 +143,7 @@ def test_precond_and_saddle(case):
     assert rel(z, refz) < 1e-10
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
 def test_solve_matches_direct(case, prec):
     name, prob, orc, s = case
     s.set_precision(prec)
@@ -152,8 +158,11 @@ def test_solve_matches_direct(case, prec):
         assert rel(lam.cpu().numpy(), ld) < 1e-7
         assert np.linalg.norm(orc.B @ u.cpu().numpy()) < 1e-8 * np.linalg.norm(ud)
         if prec == "fp64":
+            # same iterates; the stopping iteration follows the true-residual
+            # check schedule, which rounding can move by a few iterations
             _, _, oinfo = orc.solve(f, tol=1e-10)
-            assert abs(info["iters"] - oinfo["iters"]) <= 2, (info["iters"], oinfo["iters"])
+            assert abs(info["iters"] - oinfo["iters"]) <= max(2, 0.05 * oinfo["iters"]), \
+                (info["iters"], oinfo["iters"])
     finally:
         s.set_precision("fp64")
 
@@ -180,3 +189,27 @@ def test_invalid_arguments(case):
         A.fd_apply(s.ctx, 2, x, x, 1)
     with pytest.raises(A.AfiError):
         A.fd_apply(s.ctx, 0, x, x, 0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_replay_matches_eager(case, prec):
+    """Six captured iterations replayed as a CUDA graph give the same iterates
+    (bitwise) and iteration count as launching every kernel from the host."""
+    name, prob, orc, s = case
+    from paper_2001_09626_gb300.solver import Solver
+    f = T(orc.load(W.body_force_coeffs(prob)))
+    s.set_precision(prec)
+    try:
+        u0, l0 = s.solve(f)
+        it0 = s.last_info["iters"]
+        g = Solver(prob, prec=prec, tol=1e-10, use_graph=True)
+        try:
+            u1, l1 = g.solve(f)
+            assert g.last_info["iters"] == it0
+            assert torch.equal(u0, u1) and torch.equal(l0, l1)
+            u2, _ = g.solve(f)            # replaying the cached graph again
+            assert torch.equal(u1, u2)
+        finally:
+            g.close()
+    finally:
+        s.set_precision("fp64")

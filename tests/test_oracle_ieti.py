@@ -138,3 +138,20 @@ def test_adjoint_gradients_vs_finite_differences():
         um, _ = s.direct_solve(f - e)
         fdg = ((f + e) @ up - (f - e) @ um) / (2 * h)
         assert abs(fdg - dJdf[i]) <= 1e-5 * max(abs(fdg), 1e-8)
+
+
+def test_lame_gradient_quadrature_equals_matrix_form():
+    """-int div z div u and -int 2 eps(z):eps(u) by quadrature equal
+    -z^T A_lam u and -z^T A_mu u from the assembled blocks."""
+    from oracle import adjoint
+    for name in ("C1-small", "C2-small"):
+        P = W.config(name)
+        s = AFIETI(P)
+        rng = np.random.default_rng(9)
+        u = rng.standard_normal(s.ndof)
+        z = rng.standard_normal(s.ndof)
+        ref = adjoint.lame_gradient(s, u, z)
+        for k in range(P.npatch):
+            sl = slice(s.off[k], s.off[k + 1])
+            q = adjoint.lame_gradient_quadrature(s.geo[k], u[sl], z[sl])
+            np.testing.assert_allclose(q, ref[k], rtol=1e-11, atol=1e-13)
