@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "tf32", "bf16"])
+    ap.add_argument("--prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--workload", default="C2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -296,14 +296,18 @@ def run_ours(args):
     ms_plain = timed(lambda: s.solve(f), max(1, min(args.steps, 3)))
     info_plain = dict(s.last_info)
 
-    # FD apply throughput (P_A^{-1} on every patch and component)
+    # FD apply throughput (P_A^{-1} on every patch and component), one
+    # right-hand side and a batch of 8 in one launch
     r = torch.rand(s.n_dof, dtype=torch.float64, device="cuda")
-    fd_ms = {}
+    r8 = torch.rand(8, s.n_dof, dtype=torch.float64, device="cuda")
+    fd_ms, fd8_ms = {}, {}
     for prec in ("fp64", args.prec):
         s.set_precision(prec)
         for _ in range(3):
             s.fd(r)
+            s.fd(r8)
         fd_ms[prec] = timed(lambda: s.fd(r), 20)
+        fd8_ms[prec] = timed(lambda: s.fd(r8), 10)
     s.set_precision(args.prec)
 
     # dominant kernel: FP64 stiffness matvec (one launch per apply)
@@ -329,11 +333,16 @@ def run_ours(args):
                              "GBs": round(stored_bytes / (mv_ms * 1e-3) / 1e9, 1),
                              "peak_GBs": hbm, "frac": round(stored_bytes / (mv_ms * 1e-3) / 1e9 / hbm, 3)}}
     fd_bytes = 16 * s.n_dof
-    roofline_fd = {"bound": "hbm", "kernel": f"k_fd ({args.prec} local solver)",
+    fd_kernel = "k_fd_tc (tcgen05)" if args.prec in ("tf32", "bf16") else "k_fd (SIMT)"
+    roofline_fd = {"bound": "hbm", "kernel": f"{fd_kernel}, {args.prec}",
                    "achieved": round(fd_bytes / (fd_ms[args.prec] * 1e-3) / 1e9, 1),
                    "peak": hbm, "unit": "GB/s",
                    "frac": round(fd_bytes / (fd_ms[args.prec] * 1e-3) / 1e9 / hbm, 4),
-                   "traffic": traffic_record("k_fd"), "bytes_per_launch": fd_bytes}
+                   "traffic": traffic_record("k_fd_tc" if args.prec in ("tf32", "bf16") else "k_fd"),
+                   "bytes_per_launch": fd_bytes,
+                   "nrhs8": {"achieved": round(8 * fd_bytes / (fd8_ms[args.prec] * 1e-3) / 1e9, 1),
+                             "frac": round(8 * fd_bytes / (fd8_ms[args.prec] * 1e-3) / 1e9 / hbm, 4),
+                             "launch_ms": round(fd8_ms[args.prec], 4)}}
 
     line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
@@ -348,6 +357,8 @@ def run_ours(args):
             "plain_fp64": {"solve_s": round(ms_plain / 1e3, 4), "iterations": info_plain["iters"],
                            "relres_true": info_plain["relres_true"]},
             "fd_apply_dofs_per_s": {k: round(s.n_dof / (v * 1e-3), 1) for k, v in fd_ms.items()},
+            "fd_apply_dofs_per_s_nrhs8": {k: round(8 * s.n_dof / (v * 1e-3), 1)
+                                          for k, v in fd8_ms.items()},
             "e2e": {"value": round(ms_e2e / 1e3, 4), "unit": "s",
                     "h2d_bytes_per_step": 8 * s.n_dof, "d2h_bytes_per_step": 8 * s.n_dof},
             "gpu_launches": int(launches), "roofline": roofline, "roofline_fd": roofline_fd,

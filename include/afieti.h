@@ -81,12 +81,20 @@ typedef struct {
   const unsigned char *dirichlet_face;
 } afi_problem;
 
+/* afi_options.variant bits */
+#define AFI_VARIANT_LOCAL_ONLY 1   /* set up the local solvers, constraints and
+                                      projectors only: no quadrature geometry,
+                                      no stiffness (whose stencil can exceed
+                                      device memory); ieti_solve, afi_apply of
+                                      STIFFNESS/SADDLE, afi_load_vector and
+                                      afi_lame_grad then return AFI_EINVAL */
+
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
  * preconditioned residual estimate and then the true FP64 residual
  * ||b - A x|| / ||b|| of eq. (4.7) must both reach it); maxit: iteration cap;
  * use_graph: 1 runs the MINRES iterations as replays of a CUDA graph of six
  * captured iterations (same iterates and iteration count as 0, which
- * launches every kernel from the host); variant: reserved, pass 0. */
+ * launches every kernel from the host); variant: 0 or AFI_VARIANT_LOCAL_ONLY. */
 typedef struct {
   afi_fd_precision prec;
   double tol;

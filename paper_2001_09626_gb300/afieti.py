@@ -154,12 +154,15 @@ class Problem:
                              self.dface.ctypes.data_as(C.POINTER(C.c_ubyte)))
 
 
-def af_ieti_setup(prob, prec="fp64", tol=1e-8, maxit=2000, use_graph=False):
+AFI_VARIANT_LOCAL_ONLY = 1
+
+
+def af_ieti_setup(prob, prec="fp64", tol=1e-8, maxit=2000, use_graph=False, variant=0):
     """Create a context for a afi_workloads.Problem; returns the handle (int)."""
     lib = load()
     P = prob if isinstance(prob, Problem) else Problem(prob)
     opt = afi_options(PRECISIONS.get(prec, prec) if isinstance(prec, str) else int(prec),
-                      float(tol), int(maxit), 1 if use_graph else 0, 0)
+                      float(tol), int(maxit), 1 if use_graph else 0, int(variant))
     h = C.c_void_p()
     _check(lib.af_ieti_setup(C.byref(P.c), C.byref(opt), C.byref(h)), "af_ieti_setup")
     return h.value

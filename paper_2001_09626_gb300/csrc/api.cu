@@ -9,6 +9,13 @@ using namespace afi;
 
 static cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// entry points that need the assembled stiffness or the quadrature geometry
+static bool has_operator(afi_ctx *c) {
+  if (c->stencil) return true;
+  set_error("context set up with AFI_VARIANT_LOCAL_ONLY: no stiffness or geometry");
+  return false;
+}
+
 extern "C" {
 
 afi_status af_ieti_setup(const afi_problem *prob, const afi_options *opt, afi_ctx **out) {
@@ -38,15 +45,13 @@ afi_status fd_apply(afi_ctx *c, int interior, const double *r, double *s, int nr
     set_error("fd_apply: invalid argument");
     return AFI_EINVAL;
   }
-  const long len = interior ? c->n_int : c->n_dof;
-  for (int j = 0; j < nrhs; ++j)
-    AFI_TRY(fd_run(c, interior, r + (long long)j * len, s + (long long)j * len, as_stream(stream)));
-  return AFI_OK;
+  return fd_run(c, interior, r, s, as_stream(stream), nrhs);
 }
 
 static afi_status solve_many(afi_ctx *c, const double *f, double *u, double *lam, int nrhs,
                              afi_info *info, void *stream) {
   if (!c || !f || !u || nrhs < 1) { set_error("solve: invalid argument"); return AFI_EINVAL; }
+  if (!has_operator(c)) return AFI_EINVAL;
   afi_status worst = AFI_OK;
   for (int j = 0; j < nrhs; ++j) {
     afi_status st = solve_one(c, f + (long long)j * c->n_dof, u + (long long)j * c->n_dof,
@@ -69,17 +74,20 @@ afi_status ieti_solve_adjoint(afi_ctx *c, const double *g, double *z, double *zl
 
 afi_status afi_lame_grad(afi_ctx *c, const double *u, const double *z, double *grad, void *stream) {
   if (!c || !u || !z || !grad) { set_error("afi_lame_grad: invalid argument"); return AFI_EINVAL; }
+  if (!has_operator(c)) return AFI_EINVAL;
   return op_lame_grad(c, u, z, grad, as_stream(stream));
 }
 
 afi_status afi_load_vector(afi_ctx *c, const double *coef, double *f, void *stream) {
   if (!c || !coef || !f) { set_error("afi_load_vector: invalid argument"); return AFI_EINVAL; }
+  if (!has_operator(c)) return AFI_EINVAL;
   return op_load(c, coef, f, as_stream(stream));
 }
 
 afi_status afi_apply(afi_ctx *c, afi_operator op, const double *x, double *y, void *stream) {
   if (!c || !x || !y) { set_error("afi_apply: invalid argument"); return AFI_EINVAL; }
   cudaStream_t s = as_stream(stream);
+  if ((op == AFI_OP_STIFFNESS || op == AFI_OP_SADDLE) && !has_operator(c)) return AFI_EINVAL;
   switch (op) {
     case AFI_OP_STIFFNESS: return op_stiffness(c, x, y, s);
     case AFI_OP_B: return op_B(c, x, y, s);

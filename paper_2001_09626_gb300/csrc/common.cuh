@@ -62,6 +62,9 @@ struct Tab1D {
   long long Up, Upt;           // U and U^T padded to [n][ld] (zero padding)
   long long Uip, Uipt;         // interior U and U^T padded to [ni][ldi]
   long long Kb, Mb;            // bands by diagonal: Kb[t*n + i] = K[i][i + t - p], t = 0..2p
+  long long tcB[2][2][2];      // tensor-core B operands, byte offsets in tcpool:
+                               // [bf16][interior][back]; forward B[a][k] = U[k][a],
+                               // back B[i][k] = U[i][k], canonical K-major layout
 };
 
 // Per-patch descriptor (device-side POD).
@@ -80,6 +83,17 @@ struct DevPatch {
   long long qoff;   // quadrature geometry offset (points)
   long long xoff;   // control point offset (doubles)
   double lam, mu, Hs;  // Lame values, H^{d-2}
+};
+
+// Split of the patches between the tensor-core FD (tensors that fit one CTA)
+// and the SIMT FD, per (interior, operand format); built on first use.
+struct TcSplit {
+  bool ready = false;
+  int *d_tc = nullptr, *d_simt = nullptr;   // patch index lists (device)
+  int ntc = 0, nsimt = 0;
+  int cap = 0, bsz = 0, tcols = 32;
+  size_t smem = 0;
+  int simt_maxN = 0;
 };
 
 struct afi_ctx_impl;
@@ -106,6 +120,7 @@ struct afi_ctx {
   double *dpool = nullptr;  long long dpool_n = 0;
   float *fpool = nullptr;   long long fpool_n = 0;
   __nv_bfloat16 *bpool = nullptr; long long bpool_n = 0;
+  unsigned char *tcpool = nullptr; long long tcpool_n = 0;   // tensor-core B operands
   double *ctrl = nullptr;                     // all control points
   double *stencil = nullptr; long long stencil_n = 0;
   double *qgeo = nullptr; long long nqp = 0;  // [DIM*DIM + 1][nqp] SoA
@@ -143,6 +158,7 @@ struct afi_ctx {
   void *graph_exec = nullptr;
   void *cap_stream = nullptr;        // private stream used only for capture
   const double *gate = nullptr;      // while enqueueing MINRES: device 'active' flag
+  afi::TcSplit tcsplit[2][2];        // [interior][bf16]
   long long graph_nodes = 0;
   int graph_prec = -1;
 };
@@ -184,12 +200,19 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam, afi_in
                      cudaStream_t s);
 
 // fd.cu (local solvers: Algorithm 1 and the parametric Schur complement)
-afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st);
+afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st,
+                  int nrhs = 1);
 afi_status schur_run(afi_ctx *c, const double *t, double *y, cudaStream_t st);
 afi_status fd_prepare(afi_ctx *c);
-// fd_tc.cu (tensor-core FD; AFI_EINVAL if a patch tensor does not fit)
+// fd_tc.cu (tensor-core FD over the patches that fit; the others go to the
+// SIMT kernel through simt_list)
 afi_status fd_tc_prepare(afi_ctx *c);
-afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st);
+afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st,
+                     int nrhs);
+afi_status fd_simt_list(afi_ctx *c, int interior, const int *list, int count, int maxN,
+                        const double *r, double *s, cudaStream_t st, int nrhs);
+afi_status fd_tc_ready(afi_ctx *c);
+afi_status fd_tc_tables(afi_ctx *c);
 
 // reductions (ops.cu)
 afi_status dot(afi_ctx *c, const double *a, const double *b, long n, double *dst,

@@ -73,30 +73,61 @@ __device__ __forceinline__ void mode_rb(const T *__restrict__ src, T *__restrict
 
 // dst = alpha * Mat1(src1) [+ beta * Mat2(src2)] along direction d, with the
 // banded (half-bandwidth p) univariate matrices stored by diagonal:
-// Mb[t*n + i] = Mat[i][i + t - p].
-template <typename T>
-__device__ __forceinline__ void mode_band2(const T *__restrict__ src1, const T *__restrict__ Mb1,
-                                           T alpha, const T *__restrict__ src2,
-                                           const T *__restrict__ Mb2, T beta, T *__restrict__ dst,
-                                           int p, int d, int n1, int n2, int n3) {
-  const int tot = n1 * n2 * n3;
+// Mb[t*n + i] = Mat[i][i + t - p].  One thread per line along d: the line
+// base is decoded once, then the thread walks the line.  PC > 0 fixes the
+// half-bandwidth at compile time.
+template <typename T, int PC>
+__device__ __forceinline__ void mode_band2_lines(const T *__restrict__ src1,
+                                                 const T *__restrict__ Mb1, T alpha,
+                                                 const T *__restrict__ src2,
+                                                 const T *__restrict__ Mb2, T beta,
+                                                 T *__restrict__ dst, int p_rt, int d, int n1,
+                                                 int n2, int n3) {
+  const int p = PC > 0 ? PC : p_rt;
   const int n = (d == 0) ? n1 : (d == 1 ? n2 : n3);
   const int stride = (d == 0) ? 1 : (d == 1 ? n1 : n1 * n2);
-  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
-    const int io = (d == 0) ? idx % n1 : (d == 1 ? (idx / n1) % n2 : idx / (n1 * n2));
-    const int tlo = max(p - io, 0), thi = min(2 * p, p + n - 1 - io);
-    const int base = idx + (-p) * stride;   // element j = io + t - p sits at base + t*stride
-    T a1 = 0, a2 = 0;
-    if (src2) {
-      for (int t = tlo; t <= thi; ++t) {
-        a1 += Mb1[t * n + io] * src1[base + t * stride];
-        a2 += Mb2[t * n + io] * src2[base + t * stride];
+  const int nlines = n1 * n2 * n3 / n;
+  for (int line = threadIdx.x; line < nlines; line += blockDim.x) {
+    int base;
+    if (d == 0) base = line * n1;
+    else if (d == 1) base = (line % n1) + (line / n1) * n1 * n2;
+    else base = line;
+    for (int io = 0; io < n; ++io) {
+      T a1 = 0, a2 = 0;
+      const int j0 = io - p;
+#pragma unroll
+      for (int t = 0; t < (PC > 0 ? 2 * PC + 1 : 1); ++t) {
+        if (PC == 0) break;
+        const int j = j0 + t;
+        if (j >= 0 && j < n) {
+          a1 += Mb1[t * n + io] * src1[base + j * stride];
+          if (src2) a2 += Mb2[t * n + io] * src2[base + j * stride];
+        }
       }
-      dst[idx] = alpha * a1 + beta * a2;
-    } else {
-      for (int t = tlo; t <= thi; ++t) a1 += Mb1[t * n + io] * src1[base + t * stride];
-      dst[idx] = alpha * a1;
+      if (PC == 0)
+        for (int t = 0; t <= 2 * p; ++t) {
+          const int j = j0 + t;
+          if (j >= 0 && j < n) {
+            a1 += Mb1[t * n + io] * src1[base + j * stride];
+            if (src2) a2 += Mb2[t * n + io] * src2[base + j * stride];
+          }
+        }
+      dst[base + io * stride] = alpha * a1 + (src2 ? beta * a2 : T(0));
     }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void mode_band2(const T *src1, const T *Mb1, T alpha, const T *src2,
+                                           const T *Mb2, T beta, T *dst, int p, int d, int n1,
+                                           int n2, int n3) {
+  switch (p) {
+    case 1: mode_band2_lines<T, 1>(src1, Mb1, alpha, src2, Mb2, beta, dst, p, d, n1, n2, n3); break;
+    case 2: mode_band2_lines<T, 2>(src1, Mb1, alpha, src2, Mb2, beta, dst, p, d, n1, n2, n3); break;
+    case 3: mode_band2_lines<T, 3>(src1, Mb1, alpha, src2, Mb2, beta, dst, p, d, n1, n2, n3); break;
+    case 4: mode_band2_lines<T, 4>(src1, Mb1, alpha, src2, Mb2, beta, dst, p, d, n1, n2, n3); break;
+    case 5: mode_band2_lines<T, 5>(src1, Mb1, alpha, src2, Mb2, beta, dst, p, d, n1, n2, n3); break;
+    default: mode_band2_lines<T, 0>(src1, Mb1, alpha, src2, Mb2, beta, dst, p, d, n1, n2, n3);
   }
 }
 
@@ -149,14 +180,18 @@ __device__ T *fd_tensor(T *cur, T *oth, const DevPatch &pt, const Tab1D *tabs, c
 template <typename T>
 __global__ void __launch_bounds__(512) k_fd(const DevPatch *P, const Tab1D *tabs, const T *tpool,
                                             int dim, int interior, const double *r, double *s,
-                                            T *gscratch, int use_smem, const double *gate) {
+                                            T *gscratch, int use_smem, const double *gate,
+                                            long long rhs_stride, const int *plist) {
   if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int k = blockIdx.x, l = blockIdx.y;
+  const int k = plist ? plist[blockIdx.x] : blockIdx.x, l = blockIdx.y;
   const DevPatch pt = P[k];
   const Dims D = dims_of(pt, interior);
-  const long long base = (interior ? pt.ioff : pt.off) + (long long)l * D.N;
-  T *b0 = use_smem ? reinterpret_cast<T *>(smraw) : gscratch + 2 * base;
+  const long long tbase = (interior ? pt.ioff : pt.off) + (long long)l * D.N;
+  const long long base = tbase + (long long)blockIdx.z * rhs_stride;
+  // the global fallback slab is per tensor of one right-hand side: the
+  // launch uses grid.z = 1 whenever shared memory is too small
+  T *b0 = use_smem ? reinterpret_cast<T *>(smraw) : gscratch + 2 * tbase;
   T *b1 = b0 + D.N;
   for (int i = threadIdx.x; i < D.N; i += blockDim.x) b0[i] = (T)r[base + i];
   __syncthreads();
@@ -194,13 +229,6 @@ __device__ void ahat_apply(const T *v, T *out, T *t1, T *t2, const DevPatch &pt,
   __syncthreads();
 }
 
-__device__ __forceinline__ bool on_shell(int idx, const DevPatch &pt, int dim) {
-  const int i1 = idx % pt.n[0], i2 = (idx / pt.n[0]) % pt.n[1], i3 = idx / (pt.n[0] * pt.n[1]);
-  bool s = (i1 == 0 || i1 == pt.n[0] - 1 || i2 == 0 || i2 == pt.n[1] - 1);
-  if (dim == 3) s = s || (i3 == 0 || i3 == pt.n[2] - 1);
-  return s;
-}
-
 // y = H^{d-2} S_hat_l theta for every (patch, component); t, y torn vectors,
 // only shell entries of t are read, interior entries of y are zero.
 template <typename T>
@@ -215,28 +243,45 @@ __global__ void __launch_bounds__(512) k_schur(const DevPatch *P, const Tab1D *t
   const long long base = pt.off + (long long)l * N;
   T *B0 = use_smem ? reinterpret_cast<T *>(smraw) : gscratch + 4 * base;
   T *B1 = B0 + N, *B2 = B1 + N, *B3 = B2 + N;
-  for (int i = threadIdx.x; i < N; i += blockDim.x)
-    B0[i] = on_shell(i, pt, dim) ? (T)t[base + i] : T(0);
+  const int n1 = pt.n[0], n2 = pt.n[1], n3 = pt.n[2];
+  for (int line = threadIdx.x; line < n2 * n3; line += blockDim.x) {   // theta on the shell
+    const int i2 = line % n2, i3 = line / n2;
+    const bool face = i2 == 0 || i2 == n2 - 1 || (dim == 3 && (i3 == 0 || i3 == n3 - 1));
+    for (int i1 = 0; i1 < n1; ++i1) {
+      const int i = i1 + n1 * line;
+      B0[i] = (face || i1 == 0 || i1 == n1 - 1) ? (T)t[base + i] : T(0);
+    }
+  }
   __syncthreads();
   ahat_apply<T>(B0, B1, B2, B3, pt, tabs, tpool, dim, l);   // B1 = A_hat [theta; 0]
   // interior solve v_I = -(A_hat)_II^{-1} (B1)_I on compact tensors in B2/B3
   const Dims Di = dims_of(pt, 1);
   const int zoff = (dim == 3) ? 1 : 0;
-  for (int idx = threadIdx.x; idx < Di.N; idx += blockDim.x) {
-    const int j1 = idx % Di.n[0], j2 = (idx / Di.n[0]) % Di.n[1], j3 = idx / (Di.n[0] * Di.n[1]);
-    B2[idx] = B1[(j1 + 1) + pt.n[0] * ((j2 + 1) + pt.n[1] * (j3 + zoff))];
+  for (int line = threadIdx.x; line < Di.n[1] * Di.n[2]; line += blockDim.x) {
+    const int j2 = line % Di.n[1], j3 = line / Di.n[1];
+    const T *src = B1 + 1 + n1 * ((j2 + 1) + n2 * (j3 + zoff));
+    T *dstl = B2 + Di.n[0] * line;
+    for (int j1 = 0; j1 < Di.n[0]; ++j1) dstl[j1] = src[j1];
   }
   __syncthreads();
   const T *vI = fd_tensor<T>(B2, B3, pt, tabs, tpool, dim, l, 1);
-  for (int idx = threadIdx.x; idx < Di.N; idx += blockDim.x) {
-    const int j1 = idx % Di.n[0], j2 = (idx / Di.n[0]) % Di.n[1], j3 = idx / (Di.n[0] * Di.n[1]);
-    B0[(j1 + 1) + pt.n[0] * ((j2 + 1) + pt.n[1] * (j3 + zoff))] = -vI[idx];
+  for (int line = threadIdx.x; line < Di.n[1] * Di.n[2]; line += blockDim.x) {
+    const int j2 = line % Di.n[1], j3 = line / Di.n[1];
+    T *dstl = B0 + 1 + n1 * ((j2 + 1) + n2 * (j3 + zoff));
+    const T *src = vI + Di.n[0] * line;
+    for (int j1 = 0; j1 < Di.n[0]; ++j1) dstl[j1] = -src[j1];
   }
   __syncthreads();
   ahat_apply<T>(B0, B1, B2, B3, pt, tabs, tpool, dim, l);   // B1 = A_hat [theta; v_I]
-  const double hs = pt.Hs;
-  for (int i = threadIdx.x; i < N; i += blockDim.x)
-    y[base + i] = on_shell(i, pt, dim) ? hs * (double)B1[i] : 0.0;
+  const T hs = (T)pt.Hs;
+  for (int line = threadIdx.x; line < n2 * n3; line += blockDim.x) {
+    const int i2 = line % n2, i3 = line / n2;
+    const bool face = i2 == 0 || i2 == n2 - 1 || (dim == 3 && (i3 == 0 || i3 == n3 - 1));
+    for (int i1 = 0; i1 < n1; ++i1) {
+      const int i = i1 + n1 * line;
+      y[base + i] = (face || i1 == 0 || i1 == n1 - 1) ? (double)(hs * B1[i]) : 0.0;
+    }
+  }
 }
 
 // Opt the local-solver kernels into the device's full dynamic shared memory
@@ -255,15 +300,24 @@ afi_status fd_prepare(afi_ctx *c) {
 }
 
 template <typename T>
-static afi_status fd_launch(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st) {
-  int maxN = 1;
-  for (auto &p : c->hp) maxN = std::max(maxN, interior ? p.Ni : p.N);
+static afi_status fd_launch(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st,
+                            int nrhs, const int *list = nullptr, int count = 0, int maxN = 0) {
+  if (!list) {
+    count = c->npatch;
+    maxN = 1;
+    for (auto &p : c->hp) maxN = std::max(maxN, interior ? p.Ni : p.N);
+  }
   size_t smem = 2ull * maxN * sizeof(T);
   const int use_smem = smem <= (size_t)c->smem_optin;
   if (!use_smem) smem = 0;
-  launch(k_fd<T>, dim3(c->npatch, c->dim), 512, smem, st, c->patches, (const Tab1D *)c->tabs,
-         Pool<T>::get(c), c->dim, interior, r, s, reinterpret_cast<T *>(c->fdscratch), use_smem,
-         (const double *)c->gate);
+  const long long stride = interior ? c->n_int : c->n_dof;
+  // with the global scratch slab the right-hand sides go one launch each
+  const int per_launch = use_smem ? nrhs : 1;
+  for (int j = 0; j < nrhs; j += per_launch) {
+    launch(k_fd<T>, dim3(count, c->dim, per_launch), 512, smem, st, c->patches,
+           (const Tab1D *)c->tabs, Pool<T>::get(c), c->dim, interior, r + j * stride, s + j * stride,
+           reinterpret_cast<T *>(c->fdscratch), use_smem, (const double *)c->gate, stride, list);
+  }
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -280,18 +334,23 @@ static afi_status schur_launch(afi_ctx *c, const double *t, double *y, cudaStrea
   return AFI_OK;
 }
 
-afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st) {
+afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st,
+                  int nrhs) {
   switch (c->opt.prec) {
-    case AFI_FD_FP64: return fd_launch<double>(c, interior, r, s, st);
-    case AFI_FD_FP32: return fd_launch<float>(c, interior, r, s, st);
+    case AFI_FD_FP64: return fd_launch<double>(c, interior, r, s, st, nrhs);
+    case AFI_FD_FP32: return fd_launch<float>(c, interior, r, s, st, nrhs);
     case AFI_FD_TF32:
     case AFI_FD_BF16:
-      // tensor cores when every patch tensor fits the single-CTA kernel,
-      // FP32 otherwise
-      if (fd_tc_run(c, interior, r, s, st) == AFI_OK) return AFI_OK;
-      return fd_launch<float>(c, interior, r, s, st);
+      // tensor cores for the patches whose tensors fit one CTA, FP32 SIMT
+      // for the others
+      return fd_tc_run(c, interior, r, s, st, nrhs);
     default: set_error("local-solver precision not available"); return AFI_EINVAL;
   }
+}
+
+afi_status fd_simt_list(afi_ctx *c, int interior, const int *list, int count, int maxN,
+                        const double *r, double *s, cudaStream_t st, int nrhs) {
+  return fd_launch<float>(c, interior, r, s, st, nrhs, list, count, maxN);
 }
 
 // The Schur block (banded A_hat products and the interior FD between them)

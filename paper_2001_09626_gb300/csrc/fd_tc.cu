@@ -20,6 +20,8 @@
 // them to an mbarrier that all threads wait on with a bounded spin.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace afi {
 
 namespace tc {
@@ -82,6 +84,22 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// mbarrier expecting `bytes` of asynchronous copies (one arrival)
+__device__ __forceinline__ void expect_tx(uint64_t *mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+               "r"(bytes));
+}
+
+// 1D bulk copy global -> shared (TMA), completion counted on mbar; 16-byte
+// aligned addresses, size a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+      : "memory");
+}
+
 template <int FMT> struct Op;
 template <> struct Op<2> {   // TF32: FP32 storage, 4 elements per 16 bytes, 8 per MMA
   using T = float;
@@ -109,40 +127,51 @@ template <int FMT>
 __global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *tabs,
                                                const float *fpool, int dim, int interior,
                                                const double *r, double *s, int cap, int bsz,
-                                               int tcols, const double *gate, int *err) {
+                                               int tcols, const double *gate, int *err,
+                                               long long rhs_stride, const int *plist,
+                                               const unsigned char *tcpool) {
   using namespace tc;
   using T = typename Op<FMT>::T;
   constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
   if (gate && *gate == 0.0) return;
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t tma_bar;
   __shared__ uint32_t tslot;
   __shared__ int failed;
   T *buf[2] = {reinterpret_cast<T *>(smraw), reinterpret_cast<T *>(smraw) + cap};
   T *bm = reinterpret_cast<T *>(smraw) + 2 * cap;   // 6 B operands, bsz elements each
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int k = blockIdx.x, l = blockIdx.y;
+  const int k = plist[blockIdx.x], l = blockIdx.y;
   const DevPatch pt = P[k];
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = interior ? pt.ni[d] : pt.n[d];
   const int N = n[0] * n[1] * n[2];
-  const long long base = (interior ? pt.ioff : pt.off) + (long long)l * N;
+  const long long base =
+      (interior ? pt.ioff : pt.off) + (long long)l * N + (long long)blockIdx.z * rhs_stride;
 
-  // zero both operand buffers, build the six B operands from U
-  for (int i = tid; i < 2 * cap; i += blockDim.x) buf[0][i] = Op<FMT>::cvt(0.f);
-  for (int m = 0; m < 6; ++m) {
-    const int d = m % 3;
-    const Tab1D tb = tabs[pt.tab[d]];
-    const float *U = fpool + (interior ? tb.Ui : tb.U);
-    const int nd = n[d], Kp = rup(nd, KSTEP), Np = rup(nd, 16);
-    T *B = bm + m * bsz;
-    for (int i = tid; i < Np * Kp; i += blockDim.x) {
-      const int a = i / Kp, kk = i % Kp;
-      float v = 0.f;
-      if (a < nd && kk < nd) v = (m < 3) ? U[kk * nd + a] : U[a * nd + kk];
-      B[cm<FMT>(a, kk, Kp)] = Op<FMT>::cvt(v);
+  // stage the six B operands (prebuilt in the canonical layout) with TMA
+  // bulk copies while the threads zero the operand buffers
+  if (tid == 0) {
+    failed = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    uint32_t bytes[6], total = 0;
+    for (int m = 0; m < 6; ++m) {
+      const int nd = n[m % 3];
+      bytes[m] = (uint32_t)(rup(nd, 16) * rup(nd, KSTEP) * (int)sizeof(T));
+      total += bytes[m];
+    }
+    expect_tx(&tma_bar, total);
+    for (int m = 0; m < 6; ++m) {
+      const Tab1D tb = tabs[pt.tab[m % 3]];
+      bulk_g2s(bm + m * bsz, tcpool + tb.tcB[FMT == 1][interior][m >= 3], bytes[m], &tma_bar);
     }
   }
+  for (int i = tid; i < 2 * cap; i += blockDim.x) buf[0][i] = Op<FMT>::cvt(0.f);
   __syncthreads();
   // load the tensor as the first operand: line = i2 + n2 i3, k = i1
   {
@@ -151,10 +180,10 @@ __global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *t
       buf[0][cm<FMT>(idx / n[0], idx % n[0], Kp)] = Op<FMT>::cvt((float)r[base + idx]);
   }
   if (tid == 0) {
-    failed = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  if (!wait_phase(&tma_bar, 0)) failed = 1;   // B operands have landed
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
                  "r"(tcols));
@@ -241,40 +270,82 @@ __global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *t
 
 static int g_tc_dyn_max;
 
-// Launch geometry of the tensor-core FD for the context's patches; false if
-// some patch does not fit (the caller then uses the SIMT kernels).
-struct TcPlan { int cap, bsz, tcols; size_t smem; bool ok; };
+// Shared memory, B-operand size and TMEM columns the kernel needs for one
+// patch (operand format fmt: 2 = TF32, 1 = BF16).
+struct TcNeed { int cap, bsz, tcols; bool ok; };
 
-static TcPlan tc_plan(const afi_ctx *c, int interior, int fmt) {
-  const int kstep = (fmt == 2) ? 8 : 16, esz = (fmt == 2) ? 4 : 2;
-  TcPlan pl{0, 0, 32, 0, true};
-  for (const auto &p : c->hp) {
-    int n[3];
-    for (int d = 0; d < 3; ++d) n[d] = interior ? p.ni[d] : p.n[d];
-    for (int d = 0; d < 3; ++d) {
-      const int na = n[d], nb = n[(d + 1) % 3], nc = n[(d + 2) % 3];
-      const int Lp = tc::rup(nb * nc, 128), Kp = tc::rup(na, kstep), Np = tc::rup(na, 16);
-      pl.cap = std::max(pl.cap, Lp * Kp);
-      pl.bsz = std::max(pl.bsz, Np * Kp);
-      int cols = (Lp / 128) * Np;
-      while (pl.tcols < cols) pl.tcols *= 2;
-      if (Np > 256) pl.ok = false;
-    }
+static TcNeed tc_need(const DevPatch &p, int interior, int fmt) {
+  const int kstep = (fmt == 2) ? 8 : 16;
+  TcNeed t{0, 0, 32, true};
+  int n[3];
+  for (int d = 0; d < 3; ++d) n[d] = interior ? p.ni[d] : p.n[d];
+  for (int d = 0; d < 3; ++d) {
+    const int na = n[d], nb = n[(d + 1) % 3], nc = n[(d + 2) % 3];
+    const int Lp = tc::rup(nb * nc, 128), Kp = tc::rup(na, kstep), Np = tc::rup(na, 16);
+    t.cap = std::max(t.cap, Lp * Kp);
+    t.bsz = std::max(t.bsz, Np * Kp);
+    const int cols = (Lp / 128) * Np;
+    while (t.tcols < cols) t.tcols *= 2;
+    if (Np > 256) t.ok = false;
   }
-  if (pl.tcols > 512) pl.ok = false;
-  pl.cap = tc::rup(pl.cap, 256);
-  pl.bsz = tc::rup(pl.bsz, 256);
-  pl.smem = (size_t)(2 * pl.cap + 6 * pl.bsz) * esz + 1024;
-  // keep at most 512 / tcols CTAs per SM so tensor-memory allocation never waits long
-  const size_t per_sm = 228 * 1024;
-  const size_t floor_smem = per_sm * (size_t)pl.tcols / 512 + 1024;
-  pl.smem = std::max(pl.smem, floor_smem);
-  if (pl.smem > (size_t)g_tc_dyn_max) pl.ok = false;
-  return pl;
+  if (t.tcols > 512) t.ok = false;
+  return t;
 }
 
-// dynamic shared memory the tensor-core kernels may request: the opt-in
-// limit minus their static shared memory
+static size_t tc_smem(int cap, int bsz, int tcols, int fmt) {
+  const int esz = (fmt == 2) ? 4 : 2;
+  size_t smem = (size_t)(2 * tc::rup(cap, 256) + 6 * tc::rup(bsz, 256)) * esz + 1024;
+  // at most 512 / tcols CTAs per SM, so tensor-memory allocation never waits long
+  const size_t floor_smem = (size_t)228 * 1024 * (size_t)tcols / 512 + 1024;
+  return std::max(smem, floor_smem);
+}
+
+// Patches in increasing order of need join the tensor-core list while the
+// combined launch still fits; the rest go to the SIMT kernel.
+static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
+  std::vector<std::pair<size_t, int>> order;
+  for (int k = 0; k < c->npatch; ++k) {
+    const TcNeed t = tc_need(c->hp[k], interior, fmt);
+    if (t.ok) order.push_back({tc_smem(t.cap, t.bsz, t.tcols, fmt), k});
+  }
+  std::sort(order.begin(), order.end());
+  std::vector<int> tc, simt;
+  std::vector<char> in(c->npatch, 0);
+  int cap = 0, bsz = 0, tcols = 32;
+  for (auto &o : order) {
+    const TcNeed t = tc_need(c->hp[o.second], interior, fmt);
+    const int ncap = std::max(cap, t.cap), nbsz = std::max(bsz, t.bsz), ncols = std::max(tcols, t.tcols);
+    if (tc_smem(ncap, nbsz, ncols, fmt) > (size_t)g_tc_dyn_max) continue;
+    cap = ncap; bsz = nbsz; tcols = ncols;
+    in[o.second] = 1;
+  }
+  int maxN = 1;
+  for (int k = 0; k < c->npatch; ++k) {
+    if (in[k]) tc.push_back(k);
+    else {
+      simt.push_back(k);
+      maxN = std::max(maxN, interior ? c->hp[k].Ni : c->hp[k].N);
+    }
+  }
+  sp.ntc = (int)tc.size();
+  sp.nsimt = (int)simt.size();
+  sp.cap = tc::rup(cap, 256);
+  sp.bsz = tc::rup(bsz, 256);
+  sp.tcols = tcols;
+  sp.smem = tc_smem(cap, bsz, tcols, fmt);
+  sp.simt_maxN = maxN;
+  if (sp.ntc) {
+    AFI_TRY(dalloc(c, (void **)&sp.d_tc, tc.size() * sizeof(int)));
+    AFI_CUDA(cudaMemcpy(sp.d_tc, tc.data(), tc.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  if (sp.nsimt) {
+    AFI_TRY(dalloc(c, (void **)&sp.d_simt, simt.size() * sizeof(int)));
+    AFI_CUDA(cudaMemcpy(sp.d_simt, simt.data(), simt.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  sp.ready = true;
+  return AFI_OK;
+}
+
 afi_status fd_tc_prepare(afi_ctx *c) {
   cudaFuncAttributes fa2, fa1;
   AFI_CUDA(cudaFuncGetAttributes(&fa2, k_fd_tc<2>));
@@ -286,20 +357,81 @@ afi_status fd_tc_prepare(afi_ctx *c) {
   return AFI_OK;
 }
 
-// Tensor-core FD; returns AFI_EINVAL (without launching) if a patch does not fit.
-afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st) {
+// Tensor-core FD on the patches that fit, SIMT FP32 FD on the others.  The
+// splits are built outside stream capture: the first solve builds them
+// before capturing (see fd_tc_ready).
+afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st,
+                     int nrhs) {
   const int fmt = (c->opt.prec == AFI_FD_BF16) ? 1 : 2;
-  const TcPlan pl = tc_plan(c, interior, fmt);
-  if (!pl.ok) return AFI_EINVAL;
-  if (fmt == 2)
-    launch(k_fd_tc<2>, dim3(c->npatch, c->dim), 256, pl.smem, st, (const DevPatch *)c->patches,
-           (const Tab1D *)c->tabs, (const float *)c->fpool, c->dim, interior, r, s, pl.cap, pl.bsz,
-           pl.tcols, c->gate, c->dflag + 1);
-  else
-    launch(k_fd_tc<1>, dim3(c->npatch, c->dim), 256, pl.smem, st, (const DevPatch *)c->patches,
-           (const Tab1D *)c->tabs, (const float *)c->fpool, c->dim, interior, r, s, pl.cap, pl.bsz,
-           pl.tcols, c->gate, c->dflag + 1);
+  TcSplit &sp = c->tcsplit[interior][fmt == 1];
+  if (!sp.ready) AFI_TRY(build_split(c, interior, fmt, sp));
+  const long long stride = interior ? c->n_int : c->n_dof;
+  if (sp.ntc) {
+    const dim3 grid(sp.ntc, c->dim, nrhs);
+    if (fmt == 2)
+      launch(k_fd_tc<2>, grid, 256, sp.smem, st, (const DevPatch *)c->patches,
+             (const Tab1D *)c->tabs, (const float *)c->fpool, c->dim, interior, r, s, sp.cap,
+             sp.bsz, sp.tcols, c->gate, c->dflag + 1, stride, (const int *)sp.d_tc,
+             (const unsigned char *)c->tcpool);
+    else
+      launch(k_fd_tc<1>, grid, 256, sp.smem, st, (const DevPatch *)c->patches,
+             (const Tab1D *)c->tabs, (const float *)c->fpool, c->dim, interior, r, s, sp.cap,
+             sp.bsz, sp.tcols, c->gate, c->dflag + 1, stride, (const int *)sp.d_tc,
+             (const unsigned char *)c->tcpool);
+    AFI_LAUNCH_CHECK();
+  }
+  if (sp.nsimt) AFI_TRY(fd_simt_list(c, interior, sp.d_simt, sp.nsimt, sp.simt_maxN, r, s, st, nrhs));
+  return AFI_OK;
+}
+
+// The B operands of every table in the canonical K-major layout, for both
+// operand formats, full and interior pencils, forward (U^T) and back (U).
+__global__ void k_tc_bops(const Tab1D *tabs, int ntab, const double *pool, unsigned char *tcpool) {
+  const int t = blockIdx.y, v = blockIdx.z;   // v = bf16 * 4 + interior * 2 + back
+  if (t >= ntab) return;
+  const Tab1D T = tabs[t];
+  const int bf = v >> 2, in = (v >> 1) & 1, back = v & 1;
+  const int n = in ? T.ni : T.n;
+  const double *U = pool + (in ? T.Ui : T.U);
+  const int Np = tc::rup(n, 16), Kp = tc::rup(n, bf ? 16 : 8);
+  unsigned char *dst = tcpool + T.tcB[bf][in][back];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Np * Kp; i += gridDim.x * blockDim.x) {
+    const int a = i / Kp, k = i % Kp;
+    double val = 0.0;
+    if (a < n && k < n) val = back ? U[a * n + k] : U[k * n + a];
+    if (bf) reinterpret_cast<__nv_bfloat16 *>(dst)[tc::cm<1>(a, k, Kp)] = __double2bfloat16(val);
+    else reinterpret_cast<float *>(dst)[tc::cm<2>(a, k, Kp)] = (float)val;
+  }
+}
+
+afi_status fd_tc_tables(afi_ctx *c) {
+  long long off = 0;
+  for (auto &T : c->htab)
+    for (int bf = 0; bf < 2; ++bf)
+      for (int in = 0; in < 2; ++in)
+        for (int back = 0; back < 2; ++back) {
+          const int n = in ? T.ni : T.n;
+          const long long bytes = (long long)tc::rup(n, 16) * tc::rup(n, bf ? 16 : 8) * (bf ? 2 : 4);
+          T.tcB[bf][in][back] = off;
+          off += (bytes + 127) / 128 * 128;
+        }
+  c->tcpool_n = off;
+  AFI_TRY(dalloc(c, (void **)&c->tcpool, (size_t)off));
+  AFI_CUDA(cudaMemcpy(c->tabs, c->htab.data(), c->htab.size() * sizeof(Tab1D), cudaMemcpyHostToDevice));
+  const int nt = (int)c->htab.size();
+  launch(k_tc_bops, dim3(4, nt, 8), 256, 0, 0, (const Tab1D *)c->tabs, nt, (const double *)c->dpool,
+         c->tcpool);
   AFI_LAUNCH_CHECK();
+  return AFI_OK;
+}
+
+// Build every split up front (called before a CUDA graph is captured).
+afi_status fd_tc_ready(afi_ctx *c) {
+  for (int in = 0; in < 2; ++in)
+    for (int f = 1; f <= 2; ++f) {
+      TcSplit &sp = c->tcsplit[in][f == 1];
+      if (!sp.ready) AFI_TRY(build_split(c, in, f, sp));
+    }
   return AFI_OK;
 }
 

@@ -31,24 +31,30 @@ __device__ __forceinline__ double rigid(int a, int comp, const double *X, int di
 // decode a torn dof of patch k into (component, node) and fetch its point
 __device__ __forceinline__ const double *dof_point(const DevPatch &pt, const double *ctrl,
                                                    long long dof, int dim, int &comp) {
-  long long r = dof - pt.off;
-  comp = (int)(r / pt.N);
-  int node = (int)(r - (long long)comp * pt.N);
+  const int r = (int)(dof - pt.off);   // within one patch: fits in 32 bits
+  comp = r / pt.N;
+  const int node = r - comp * pt.N;
   return ctrl + pt.xoff + (long long)node * dim;
 }
 
 template <int NT>
 __device__ __forceinline__ void block_sum_multi(double *vals, int nv, double *sh) {
-  // sums vals[0..nv) over the block in a fixed order; result in vals on
-  // thread 0.  sh: NT * nv doubles of shared scratch.
-  for (int i = 0; i < nv; ++i) sh[i * NT + threadIdx.x] = vals[i];
-  __syncthreads();
-  for (int s = NT / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int i = 0; i < nv; ++i) sh[i * NT + threadIdx.x] += sh[i * NT + threadIdx.x + s];
-    __syncthreads();
+  // sums vals[0..nv) over the block in a fixed order (warp shuffles, then
+  // the per-warp sums in warp order); result in vals on thread 0.
+  // sh: (NT / 32) * nv doubles of shared scratch.
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = 0; i < nv; ++i) {
+    double v = vals[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[i * (NT / 32) + warp] = v;
   }
-  for (int i = 0; i < nv; ++i) vals[i] = sh[i * NT];
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nv; ++i) {
+      double v = 0.0;
+      for (int w = 0; w < NT / 32; ++w) v += sh[i * (NT / 32) + w];
+      vals[i] = v;
+    }
   __syncthreads();
 }
 
@@ -215,15 +221,18 @@ constexpr int kGtBlocks = 8;    // blocks per patch for the row-list reduction
 constexpr int kRtChunks = 16;   // blocks per (patch, component) for R^T v
 
 // Partial sums of (G^T x) over a strided part of the rows touching patch k:
-// part[(k * kGtBlocks + b) * NM + a].
+// part[(k * kGtBlocks + b) * NM + a].  Each entry touches its translation
+// and two rotations only (rigid_nz); the lists are sorted by dof, so a warp
+// mostly sees one component.
 template <int NM>
 __global__ void __launch_bounds__(256) k_Gt_part(const DevPatch *P, const double *ctrl,
                                                  const int *ptr, const int2 *ent, const double *x,
                                                  double *part, int dim) {
-  __shared__ double sh[256 * NM];
+  __shared__ double sh[8 * NM];
   const int k = blockIdx.y, b = blockIdx.x;
   const DevPatch pt = P[k];
   double acc[NM];
+#pragma unroll
   for (int a = 0; a < NM; ++a) acc[a] = 0.0;
   for (int e = ptr[k] + b * blockDim.x + threadIdx.x; e < ptr[k + 1]; e += gridDim.x * blockDim.x) {
     int2 en = ent[e];
@@ -231,7 +240,14 @@ __global__ void __launch_bounds__(256) k_Gt_part(const DevPatch *P, const double
     if (en.x & 1) xv = -xv;
     int comp;
     const double *X = dof_point(pt, ctrl, en.y, dim, comp);
-    for (int a = 0; a < NM; ++a) acc[a] += xv * rigid(a, comp, X, dim);
+    if (NM == 6) {
+      if (comp == 0) { acc[0] += xv; acc[4] += xv * X[2]; acc[5] += xv * X[1]; }
+      else if (comp == 1) { acc[1] += xv; acc[3] += xv * X[2]; acc[5] -= xv * X[0]; }
+      else { acc[2] += xv; acc[3] -= xv * X[1]; acc[4] -= xv * X[0]; }
+    } else {
+      if (comp == 0) { acc[0] += xv; acc[2] += xv * X[1]; }
+      else { acc[1] += xv; acc[2] -= xv * X[0]; }
+    }
   }
   block_sum_multi<256>(acc, NM, sh);
   if (threadIdx.x == 0)
@@ -263,7 +279,7 @@ __global__ void k_part_final(const double *part, int nb, int nm, int npatch, dou
 // translation and the two rotation products, part[((k*dim + comp)*CH + ch)*3].
 __global__ void __launch_bounds__(256) k_Rt_part(const DevPatch *P, const double *ctrl,
                                                  const double *v, double *part, int dim) {
-  __shared__ double sh[256 * 3];
+  __shared__ double sh[8 * 3];
   const int ch = blockIdx.x, comp = blockIdx.y, k = blockIdx.z;
   const DevPatch pt = P[k];
   const double *vc = v + pt.off + (long long)comp * pt.N;
@@ -281,29 +297,35 @@ __global__ void __launch_bounds__(256) k_Rt_part(const DevPatch *P, const double
     for (int a = 0; a < 3; ++a) part[(((long long)k * dim + comp) * gridDim.x + ch) * 3 + a] = acc[a];
 }
 
-// g[k][a] from the R^T v partials (fixed order), optionally y = Minv_k g_k.
+// g[k][a] from the R^T v partials, optionally y = Minv_k g_k.  One warp per
+// patch: lanes sum the chunks of each (component, product) in a fixed order.
 __global__ void k_Rt_final(const double *part, int nch, int dim, int nm, int npatch, double *g,
                            const double *Minv) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (k >= npatch) return;
   double t[6] = {0, 0, 0, 0, 0, 0};
   const double X0[3] = {0.0, 0.0, 0.0};
   for (int comp = 0; comp < dim; ++comp) {
     const RigidNZ r = rigid_nz(comp, X0, dim);   // only the mode indices are used
-    for (int ch = 0; ch < nch; ++ch) {
-      const double *q = part + (((long long)k * dim + comp) * nch + ch) * 3;
-      t[comp] += q[0];
-      t[r.m1] += q[1];
-      if (dim == 3) t[r.m2] += q[2];
-    }
+    double q[3] = {0.0, 0.0, 0.0};
+    for (int ch = lane; ch < nch; ch += 32)
+      for (int a = 0; a < 3; ++a) q[a] += part[(((long long)k * dim + comp) * nch + ch) * 3 + a];
+    for (int a = 0; a < 3; ++a)
+      for (int o = 16; o > 0; o >>= 1) q[a] += __shfl_xor_sync(0xffffffffu, q[a], o);
+    t[comp] += q[0];
+    t[r.m1] += q[1];
+    if (dim == 3) t[r.m2] += q[2];
   }
-  for (int a = 0; a < nm; ++a) {
-    double v = t[a];
+  if (lane < nm) {
+    double v;
     if (Minv) {
       v = 0.0;
-      for (int b = 0; b < nm; ++b) v += Minv[((long long)k * nm + a) * nm + b] * t[b];
+      for (int b = 0; b < nm; ++b) v += Minv[((long long)k * nm + lane) * nm + b] * t[b];
+    } else {
+      v = (lane == 0) ? t[0] : (lane == 1) ? t[1] : (lane == 2) ? t[2] : (lane == 3) ? t[3]
+          : (lane == 4) ? t[4] : t[5];
     }
-    g[k * nm + a] = v;
+    g[k * nm + lane] = v;
   }
 }
 
@@ -332,24 +354,32 @@ __global__ void k_dense_mv(const double *M, const double *g, double *y, int n) {
   if (lane == 0) y[row] = s;
 }
 
+// (R_k y_k) at one dof: its translation plus two rotations (one in 2D).
+__device__ __forceinline__ double rigid_apply(int comp, const double *X, const double *y, int dim) {
+  const RigidNZ r = rigid_nz(comp, X, dim);
+  double v = y[comp] + r.v1 * y[r.m1];
+  if (dim == 3) v += r.v2 * y[r.m2];
+  return v;
+}
+
 // out[r] (= or -=) sum over the row's copies of sign * (R_k y_k)(copy).
 __global__ void k_G(const DevPatch *P, const double *ctrl, const int2 *rc, const int2 *rk, long n_c,
                     const double *y, double *out, int dim, int nm, int subtract, const double *src) {
   long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= n_c) return;
   int2 e = rc[r], kk = rk[r];
-  double v = 0.0;
+  double v;
   {
     const DevPatch pa = P[kk.x];
     int comp;
     const double *X = dof_point(pa, ctrl, e.x, dim, comp);
-    for (int a = 0; a < nm; ++a) v += rigid(a, comp, X, dim) * y[kk.x * nm + a];
+    v = rigid_apply(comp, X, y + kk.x * nm, dim);
   }
   if (e.y >= 0) {
     const DevPatch pb = P[kk.y];
     int comp;
     const double *X = dof_point(pb, ctrl, e.y, dim, comp);
-    for (int a = 0; a < nm; ++a) v -= rigid(a, comp, X, dim) * y[kk.y * nm + a];
+    v -= rigid_apply(comp, X, y + kk.y * nm, dim);
   }
   out[r] = subtract ? src[r] - v : v;
 }
@@ -367,8 +397,8 @@ afi_status op_Gt_rows(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
 // g = R^T v per patch; with Minv, g = Minv_k (R_k^T v) instead.
 static afi_status Rt_apply(afi_ctx *c, const double *x, double *g, const double *Minv, cudaStream_t s) {
   launch(k_Rt_part, dim3(kRtChunks, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x, c->part, c->dim);
-  launch(k_Rt_final, (c->npatch + 127) / 128, 128, 0, s, (const double *)c->part, kRtChunks, c->dim,
-         c->nm, c->npatch, g, Minv);
+  launch(k_Rt_final, (c->npatch * 32 + 127) / 128, 128, 0, s, (const double *)c->part, kRtChunks,
+         c->dim, c->nm, c->npatch, g, Minv);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -780,7 +810,10 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   launch(k_minres_init, 1, 1, 0, s, st, (double)c->opt.maxit);
   AFI_LAUNCH_CHECK();
   const bool use_graph = c->opt.use_graph != 0;
-  if (use_graph) AFI_TRY(ensure_graph(c, M));
+  if (use_graph) {
+    AFI_TRY(fd_tc_ready(c));   // no allocation or host copy during capture
+    AFI_TRY(ensure_graph(c, M));
+  }
   double *hs = c->host_small;
   AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
   AFI_CUDA(cudaStreamSynchronize(s));

@@ -281,14 +281,20 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   AFI_TRY(fd_prepare(c));
   AFI_TRY(fd_tc_prepare(c));
   AFI_TRY(build_1d_tables(c));
+  AFI_TRY(fd_tc_tables(c));
   launch(k_patch_H, NP, 256, 0, 0, c->patches, c->ctrl, D);
   AFI_LAUNCH_CHECK();
   AFI_CUDA(cudaMemcpy(c->hp.data(), c->patches, NP * sizeof(DevPatch), cudaMemcpyDeviceToHost));
-  AFI_TRY(dalloc(c, (void **)&c->qgeo, (size_t)(D * D + 1) * qoff * sizeof(double)));
-  AFI_TRY(compute_geometry(c));
-  AFI_TRY(dalloc(c, (void **)&c->stencil, (size_t)soff * sizeof(double)));
-  AFI_CUDA(cudaMemset(c->stencil, 0, (size_t)soff * sizeof(double)));   // padded nodes stay 0
-  AFI_TRY(assemble_stiffness(c));
+  if (!(opt->variant & AFI_VARIANT_LOCAL_ONLY)) {
+    AFI_TRY(dalloc(c, (void **)&c->qgeo, (size_t)(D * D + 1) * qoff * sizeof(double)));
+    AFI_TRY(compute_geometry(c));
+    AFI_TRY(dalloc(c, (void **)&c->stencil, (size_t)soff * sizeof(double)));
+    AFI_CUDA(cudaMemset(c->stencil, 0, (size_t)soff * sizeof(double)));   // padded nodes stay 0
+    AFI_TRY(assemble_stiffness(c));
+  } else {
+    c->nqp = 0;
+    c->stencil_n = 0;
+  }
 
   // ---- connectivity: group interface control points by coordinates
   double scale = 0.0;
@@ -397,7 +403,11 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   std::vector<int> pptr(1, 0);
   std::vector<int2> pent;
   for (int k = 0; k < NP; ++k) {
-    for (auto &e : plist[k]) pent.push_back(make_int2(e.w, e.x));
+    std::vector<int4> lst = plist[k];
+    std::sort(lst.begin(), lst.end(), [](const int4 &a, const int4 &b) {   // by dof: by component
+      return a.x != b.x ? a.x < b.x : a.w < b.w;
+    });
+    for (auto &e : lst) pent.push_back(make_int2(e.w, e.x));
     pptr.push_back((int)pent.size());
   }
   AFI_TRY(upload(c, &c->row_copy, rc));
@@ -483,11 +493,13 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
 void free_context(afi_ctx *c) {
   if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
   if (c->cap_stream) cudaStreamDestroy((cudaStream_t)c->cap_stream);
-  void *ptrs[] = {c->patches, c->tabs, c->dpool, c->fpool, c->bpool, c->ctrl, c->stencil,
+  void *ptrs[] = {c->patches, c->tabs, c->dpool, c->fpool, c->bpool, c->tcpool, c->ctrl, c->stencil,
                   c->qgeo, c->row_copy, c->row_grp, c->row_patch, c->shell_dof, c->bt_ptr,
                   c->bt_ent, c->prow_ptr, c->prow_ent, c->pair_ptr, c->pair_kk, c->pair_ent,
                   c->GtG, c->GtG_inv, c->RtR_inv, c->ws, c->fdscratch, c->small, c->part,
-                  c->dflag};
+                  c->dflag, c->tcsplit[0][0].d_tc, c->tcsplit[0][0].d_simt, c->tcsplit[0][1].d_tc,
+                  c->tcsplit[0][1].d_simt, c->tcsplit[1][0].d_tc, c->tcsplit[1][0].d_simt,
+                  c->tcsplit[1][1].d_tc, c->tcsplit[1][1].d_simt};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);

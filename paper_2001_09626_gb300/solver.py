@@ -13,7 +13,8 @@ from . import afieti as _a
 
 
 class Solver:
-    def __init__(self, problem, prec="fp64", tol=1e-8, maxit=2000, device=None, use_graph=False):
+    def __init__(self, problem, prec="fp64", tol=1e-8, maxit=2000, device=None, use_graph=False,
+                 local_only=False):
         if not torch.cuda.is_available():
             raise RuntimeError("libafieti needs a CUDA device")
         self.device = torch.device(device or "cuda")
@@ -21,7 +22,8 @@ class Solver:
         with torch.cuda.device(self.device):
             self._P = _a.Problem(problem)
             self.ctx = _a.af_ieti_setup(self._P, prec=prec, tol=tol, maxit=maxit,
-                                        use_graph=use_graph)
+                                        use_graph=use_graph,
+                                        variant=_a.AFI_VARIANT_LOCAL_ONLY if local_only else 0)
         self.n_dof, self.n_c = _a.afi_sizes(self.ctx)
         self.last_info = None
 
@@ -63,6 +65,7 @@ class Solver:
         return y
 
     def fd(self, r, interior=False):
+        """P_A^{-1} r (or the interior solves) for one vector or a batch [nrhs, n]."""
         s = torch.empty_like(r)
         nrhs = 1 if r.dim() == 1 else r.shape[0]
         _a.fd_apply(self.ctx, 1 if interior else 0, r.contiguous(), s, nrhs)

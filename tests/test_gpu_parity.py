@@ -213,3 +213,23 @@ def test_graph_replay_matches_eager(case, prec):
             g.close()
     finally:
         s.set_precision("fp64")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
+def test_fd_batched_rhs(case, prec):
+    """fd_apply on a batch of right-hand sides (one launch) equals the
+    applications one by one."""
+    _, prob, orc, s = case
+    s.set_precision(prec)
+    try:
+        R = T(W.torn_random(prob, 41, nrhs=3))
+        batch = s.fd(R)
+        for j in range(3):
+            assert torch.equal(batch[j], s.fd(R[j].contiguous()))
+        Ri = T(np.random.default_rng(2).uniform(-1, 1, (2, sum(int(m.sum()) * orc.dim
+                                                             for _, m, _ in orc._local()))))
+        bi = s.fd(Ri, interior=True)
+        for j in range(2):
+            assert torch.equal(bi[j], s.fd(Ri[j].contiguous(), interior=True))
+    finally:
+        s.set_precision("fp64")
