@@ -220,6 +220,8 @@ def config(name: str, seed: int = 0) -> Problem:
         return quarter_annulus((3, 2, 2), 3, 3, name=name)
     if name == "C5-small":
         return twisted_box((2, 2, 2), 4, 3, name=name)
+    if name == "C5-mid":   # C5 patches (p=4, 48^3 elements), 2x2x2 of them
+        return twisted_box((2, 2, 2), 4, 48, name=name)
     if name == "C1-small":
         return unit_box(2, (2, 2), 2, 3, name=name)
     raise KeyError(name)

@@ -52,6 +52,13 @@ def parse():
     ap.add_argument("--prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--workload", default="C2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fd-only", action="store_true",
+                    help="time only the FD local solvers (P_A^{-1} and the interior solves) "
+                         "on a local-solvers-only context of --workload")
+    ap.add_argument("--nrhs", type=int, default=8, help="batch size of the --fd-only batched line")
+    ap.add_argument("--fd-slab", action="store_true",
+                    help="--fd-only: send every tensor through the three-pass kernels")
+    ap.add_argument("--precs", default="fp64,fp32,tf32,bf16", help="--fd-only: precisions to time")
     return ap.parse_args()
 
 
@@ -375,10 +382,72 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_fd_only(args):
+    """FD-apply throughput on a local-solvers-only context (no stiffness, no
+    constraints): DoF/s and the HBM roofline of the 16 B/DoF algorithmic
+    traffic, for one right-hand side and a batch, every precision."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import afi_workloads as W
+    from paper_2001_09626_gb300.solver import Solver
+    prob = W.config(args.workload)
+    s = Solver(prob, prec=args.prec, tol=1e-8, local_only=True, fd_slab=args.fd_slab)
+    stream = torch.cuda.current_stream()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    n_int = 0
+    for k in range(prob.npatch):
+        m = 1
+        for n in prob.n(k):
+            m *= n - 2
+        n_int += prob.dim * m
+    out = {}
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    for prec in args.precs.split(","):
+        s.set_precision(prec)
+        row = {}
+        for interior, n in ((False, s.n_dof), (True, n_int)):
+            for nrhs in (1, args.nrhs):
+                r = torch.rand((nrhs, n) if nrhs > 1 else (n,), dtype=torch.float64,
+                               device="cuda", generator=gen)
+                for _ in range(max(3, args.warmup)):
+                    s.fd(r, interior=interior)
+                ms = timed(lambda: s.fd(r, interior=interior), max(5, args.steps))
+                dofs = nrhs * n
+                row[f"{'interior' if interior else 'PA_inv'}_nrhs{nrhs}"] = {
+                    "ms": round(ms, 4), "dofs_per_s": round(dofs / (ms * 1e-3), 1),
+                    "GBs": round(16 * dofs / (ms * 1e-3) / 1e9, 1),
+                    "frac_hbm": round(16 * dofs / (ms * 1e-3) / 1e9 / hbm, 4)}
+        out[prec] = row
+    line = {"metric": "FD-apply DoF/s", "unit": "DoF/s", "workload": args.workload,
+            "path": "three-pass (forced)" if args.fd_slab else "automatic",
+            "n_dof": s.n_dof, "n_int": n_int, "hbm_peak_GBs": hbm, "fd": out}
+    print(json.dumps(line), flush=True)
+    s.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.fd_only:
+        run_fd_only(args)
     else:
         run_ours(args)
 

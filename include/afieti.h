@@ -88,13 +88,19 @@ typedef struct {
                                       device memory); ieti_solve, afi_apply of
                                       STIFFNESS/SADDLE, afi_load_vector and
                                       afi_lame_grad then return AFI_EINVAL */
+#define AFI_VARIANT_FD_SLAB 2      /* TF32/BF16 local solvers: send every 3D
+                                      tensor through the three-pass kernels
+                                      used for tensors larger than one CTA
+                                      (same operator; for testing and
+                                      measuring that path on small patches) */
 
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
  * preconditioned residual estimate and then the true FP64 residual
  * ||b - A x|| / ||b|| of eq. (4.7) must both reach it); maxit: iteration cap;
  * use_graph: 1 runs the MINRES iterations as replays of a CUDA graph of six
  * captured iterations (same iterates and iteration count as 0, which
- * launches every kernel from the host); variant: 0 or AFI_VARIANT_LOCAL_ONLY. */
+ * launches every kernel from the host); variant: 0 or a combination of the
+ * AFI_VARIANT_* bits. */
 typedef struct {
   afi_fd_precision prec;
   double tol;

@@ -43,6 +43,41 @@ inline void launch(Kernel kernel, dim3 grid, dim3 block, size_t smem, cudaStream
   kernel<<<grid, block, smem, stream>>>(args...);
 }
 
+// ------------------------------------------- FP64 <-> FP32 on the integer pipes
+// The mixed-precision kernels convert every FP64 input to FP32 and every
+// FP32 result back to FP64.  The hardware conversions issue on the FP64
+// pipe, which on this GPU has a small fraction of the FP32 and integer
+// issue rate, so these do the same conversions with integer operations on
+// the IEEE-754 bit fields.
+//
+// f64 -> f32: round to nearest even; results below the FP32 normal range
+// flush to signed zero, finite values above it become +-inf, NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int ein = (int)((hi >> 20) & 0x7FFu);
+  const int e = ein - 1023 + 127;
+  unsigned r = sign | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rbit = (lo >> 28) & 1u, sticky = lo & 0x0FFFFFFFu;
+  r += rbit & ((sticky != 0u) | (r & 1u));   // a carry into the exponent is correct
+  r = (e <= 0) ? sign : r;
+  r = (e >= 255 || ((r >> 23) & 0xFFu) == 0xFFu) ? (sign | 0x7F800000u) : r;
+  r = (ein == 0x7FF && (((hi & 0xFFFFFu) | lo) != 0u)) ? 0x7FC00000u : r;
+  return __uint_as_float(r);
+}
+
+// f32 -> f64: exact for normal numbers, zero and infinities; FP32
+// subnormals flush to signed zero, NaN stays NaN.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  if (e == 0xFFu) hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // ------------------------------------------------------- 1D spline tables
 // One table per distinct (nel, p) pair (open uniform knots).  Offsets index
 // the context's FP64 pool (and FP32 / BF16 pools for the low-precision
@@ -94,6 +129,11 @@ struct TcSplit {
   int cap = 0, bsz = 0, tcols = 32;
   size_t smem = 0;
   int simt_maxN = 0;
+  // three-pass tensor-core FD for tensors larger than one CTA (fd_slab.cu)
+  void *d_plane = nullptr, *d_line = nullptr;   // int4 / int2 work lists
+  int nplane = 0, nline = 0;
+  int cap_p = 0, bsz_p = 0, tcols_p = 32, cap_l = 0, bsz_l = 0, tcols_l = 32;
+  size_t smem_p = 0, smem_l = 0;
 };
 
 struct afi_ctx_impl;
@@ -213,6 +253,12 @@ afi_status fd_simt_list(afi_ctx *c, int interior, const int *list, int count, in
                         const double *r, double *s, cudaStream_t st, int nrhs);
 afi_status fd_tc_ready(afi_ctx *c);
 afi_status fd_tc_tables(afi_ctx *c);
+// fd_slab.cu (three-pass tensor-core FD for tensors larger than one CTA)
+afi_status slab_prepare(afi_ctx *c, int *dyn_max);
+afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> &cand,
+                      std::vector<int> &rest, TcSplit &sp, int dyn_max);
+afi_status slab_run(afi_ctx *c, int interior, int fmt, const TcSplit &sp, const double *r,
+                    double *s, cudaStream_t st, int nrhs);
 
 // reductions (ops.cu)
 afi_status dot(afi_ctx *c, const double *a, const double *b, long n, double *dst,

@@ -36,6 +36,34 @@ template <> struct Vec4<double> {
   }
 };
 
+// FP64 vector entries to and from the working precision (integer-pipe
+// conversions for FP32)
+template <typename T> __device__ __forceinline__ T from_f64(double x);
+template <> __device__ __forceinline__ double from_f64<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_f64<float>(double x) { return f64_to_f32(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
+__device__ __forceinline__ double to_f64(float x) { return f32_to_f64(x); }
+
+// dst[i] = src[i] (converted) for i < n, block-strided; the global loads of
+// a batch are issued before its stores so that they overlap
+template <typename T>
+__device__ __forceinline__ void load_block(const double *__restrict__ src, T *dst, int n) {
+  constexpr int LB = 8;
+  for (int i0 = threadIdx.x; i0 < n; i0 += LB * blockDim.x) {
+    double v[LB];
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = i < n ? __ldg(src + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n) dst[i] = from_f64<T>(v[u]);
+    }
+  }
+}
+
 constexpr int RA = 4;
 
 // dst[.., a, ..] = sum_j Mp[j][a] src[.., j, ..] along direction d, Mp padded
@@ -193,10 +221,10 @@ __global__ void __launch_bounds__(512) k_fd(const DevPatch *P, const Tab1D *tabs
   // launch uses grid.z = 1 whenever shared memory is too small
   T *b0 = use_smem ? reinterpret_cast<T *>(smraw) : gscratch + 2 * tbase;
   T *b1 = b0 + D.N;
-  for (int i = threadIdx.x; i < D.N; i += blockDim.x) b0[i] = (T)r[base + i];
+  load_block<T>(r + base, b0, D.N);
   __syncthreads();
   const T *res = fd_tensor<T>(b0, b1, pt, tabs, tpool, dim, l, interior);
-  for (int i = threadIdx.x; i < D.N; i += blockDim.x) s[base + i] = (double)res[i];
+  for (int i = threadIdx.x; i < D.N; i += blockDim.x) s[base + i] = to_f64(res[i]);
 }
 
 // A_hat_l v (Kronecker form) from buffer v into `out`, using two temporaries.
@@ -244,12 +272,16 @@ __global__ void __launch_bounds__(512) k_schur(const DevPatch *P, const Tab1D *t
   T *B0 = use_smem ? reinterpret_cast<T *>(smraw) : gscratch + 4 * base;
   T *B1 = B0 + N, *B2 = B1 + N, *B3 = B2 + N;
   const int n1 = pt.n[0], n2 = pt.n[1], n3 = pt.n[2];
-  for (int line = threadIdx.x; line < n2 * n3; line += blockDim.x) {   // theta on the shell
-    const int i2 = line % n2, i3 = line / n2;
-    const bool face = i2 == 0 || i2 == n2 - 1 || (dim == 3 && (i3 == 0 || i3 == n3 - 1));
-    for (int i1 = 0; i1 < n1; ++i1) {
-      const int i = i1 + n1 * line;
-      B0[i] = (face || i1 == 0 || i1 == n1 - 1) ? (T)t[base + i] : T(0);
+  // theta on the shell: the whole block is read (interior entries of t are
+  // finite: zero or stale operator output) and the interior is zeroed after
+  load_block<T>(t + base, B0, N);
+  __syncthreads();
+  {
+    const Dims Dz = dims_of(pt, 1);
+    const int zo = (dim == 3) ? 1 : 0;
+    for (int idx = threadIdx.x; idx < Dz.N; idx += blockDim.x) {
+      const int j1 = idx % Dz.n[0], j2 = (idx / Dz.n[0]) % Dz.n[1], j3 = idx / (Dz.n[0] * Dz.n[1]);
+      B0[(j1 + 1) + n1 * ((j2 + 1) + n2 * (j3 + zo))] = T(0);
     }
   }
   __syncthreads();
@@ -279,7 +311,7 @@ __global__ void __launch_bounds__(512) k_schur(const DevPatch *P, const Tab1D *t
     const bool face = i2 == 0 || i2 == n2 - 1 || (dim == 3 && (i3 == 0 || i3 == n3 - 1));
     for (int i1 = 0; i1 < n1; ++i1) {
       const int i = i1 + n1 * line;
-      y[base + i] = (face || i1 == 0 || i1 == n1 - 1) ? (double)(hs * B1[i]) : 0.0;
+      y[base + i] = (face || i1 == 0 || i1 == n1 - 1) ? to_f64(hs * B1[i]) : 0.0;
     }
   }
 }

@@ -1,0 +1,545 @@
+// Fast diagonalization (Algorithm 1, eqs. 5.6, 5.9, 5.10) on tcgen05 tensor
+// cores for tensors too large for one CTA's shared memory.  The six mode
+// products are grouped into three passes over an FP32 scratch copy of the
+// tensor X[i3][i2][i1]:
+//
+//   pass A (k_fd_plane<.., 0>): for a group of consecutive i3 planes, the
+//     products with U_1^T and U_2^T (both in one CTA, shared memory between
+//     them); reads FP64, writes FP32;
+//   pass B (k_fd_line): for a tile of 128 (a1, a2) lines, the product with
+//     U_3^T along i3, the scaling by Lambda^{-1}, and the product with U_3,
+//     in place in the scratch;
+//   pass C (k_fd_plane<.., 1>): for a group of planes, the products with U_1
+//     and U_2; reads FP32, writes FP64.
+//
+// Every pass reads and writes whole rows of 128-byte sectors, so the traffic
+// is 8 + 4 + 4 + 4 + 4 + 8 = 32 bytes per DoF (TF32/BF16 operands, FP32
+// scratch) against the 16 of a single-pass kernel.  Each MMA is a GEMM
+// D[line][j] = sum_k A[line][k] B[j][k] with the tensor as the K-major A
+// operand (lines on the 128 TMEM lanes) and U^T or U as B, staged by TMA.
+#include "tc.cuh"
+
+#include <algorithm>
+#include <type_traits>
+
+namespace afi {
+
+using namespace tc;
+
+namespace {
+
+// Issue the MMAs of one product: ntile tiles of 128 lines of the padded
+// tensor operand A (K-major, kLBO-padded), against the canonical B operand
+// (Np x Kp) at b, accumulating into TMEM columns t * Np.
+template <int FMT>
+__device__ __forceinline__ void issue_product(uint32_t tmem, const void *A, const void *B, int ntile,
+                                              int Kp, int Np) {
+  constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t id = idesc(FMT, 128, Np);
+  const int kch = Kp / T16;
+  const uint32_t sboA = (uint32_t)kch * kLBO, sboB = (uint32_t)kch * 128u;
+  const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+  for (int t = 0; t < ntile; ++t)
+    for (int ks = 0; ks < Kp / KSTEP; ++ks)
+      mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 16 * sboA + ks * 2 * kLBO, kLBO, sboA),
+               sdesc(b0 + ks * 256, 128, sboB), id, ks > 0 ? 1u : 0u);
+}
+
+// Stage the B operands of two products (prebuilt canonical layout in
+// tcpool) into slots bm and bm + bsz, and start the operand-buffer fill.
+template <typename T>
+__device__ __forceinline__ void stage_b(uint64_t *bar, T *bm, int bsz, const unsigned char *tcpool,
+                                        long long off0, uint32_t bytes0, long long off1,
+                                        uint32_t bytes1) {
+  expect_tx(bar, bytes0 + bytes1);
+  bulk_g2s(bm, tcpool + off0, bytes0, bar);
+  bulk_g2s(bm + bsz, tcpool + off1, bytes1, bar);
+}
+
+__device__ __forceinline__ float ld_in(const double *p) { return f64_to_f32(__ldg(p)); }
+__device__ __forceinline__ float ld_in(const float *p) { return __ldg(p); }
+__device__ __forceinline__ void st_out(double *p, float v) { *p = f32_to_f64(v); }
+__device__ __forceinline__ void st_out(float *p, float v) { *p = v; }
+
+}  // namespace
+
+// Passes A (BACK = 0: U_1^T then U_2^T, FP64 in, FP32 out) and C (BACK = 1:
+// U_1 then U_2, FP32 in, FP64 out) on nz planes of one (patch, component,
+// right-hand side) tensor.  work[blockIdx.x] = (patch, first plane, nz).
+template <int FMT, int BACK>
+__global__ void __launch_bounds__(256, 2) k_fd_plane(const DevPatch *P, const Tab1D *tabs,
+                                                     const int4 *work, int interior,
+                                                     const double *r, float *scr, double *s,
+                                                     long long rhs_stride, int cap, int bsz,
+                                                     int tcols, const double *gate, int *err,
+                                                     const unsigned char *tcpool) {
+  using T = typename Op<FMT>::T;
+  using TIn = typename std::conditional<BACK == 0, double, float>::type;
+  constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t tma_bar;
+  __shared__ uint32_t tslot;
+  __shared__ int failed;
+  T *A = reinterpret_cast<T *>(smraw);
+  T *bm = A + cap;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double gv = gate ? *gate : 1.0;
+  const int4 w = work[blockIdx.x];
+  const int l = blockIdx.y;
+  const DevPatch pt = P[w.x];
+  if (gv == 0.0) return;   // inactive MINRES iteration
+  const int n1 = interior ? pt.ni[0] : pt.n[0], n2 = interior ? pt.ni[1] : pt.n[1];
+  const int n3 = interior ? pt.ni[2] : pt.n[2];
+  const int z0 = w.y, nz = w.z;
+  const long long plane = (long long)n1 * n2;
+  const long long base = (interior ? pt.ioff : pt.off) + (long long)l * plane * n3 +
+                         (long long)blockIdx.z * rhs_stride + z0 * plane;
+  const TIn *in = BACK ? (const TIn *)(const void *)(scr + base) : (const TIn *)(const void *)(r + base);
+
+  if (tid == 0) {
+    failed = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  if (tid == 0)
+    stage_b(&tma_bar, bm, bsz, tcpool, tabs[pt.tab[0]].tcB[FMT == 1][interior][BACK],
+            (uint32_t)(rup(n1, 16) * rup(n1, KSTEP) * (int)sizeof(T)),
+            tabs[pt.tab[1]].tcB[FMT == 1][interior][BACK],
+            (uint32_t)(rup(n2, 16) * rup(n2, KSTEP) * (int)sizeof(T)));
+  {
+    uint4 *zp = reinterpret_cast<uint4 *>(A);
+    const int nzero = cap * (int)sizeof(T) / 16;
+    for (int i = tid; i < nzero; i += 256) zp[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  __syncthreads();
+  // first operand: row = i2 + n2 * zl, k = i1 (the slice is contiguous)
+  {
+    const int kch = rup(n1, KSTEP) / T16, N = (int)(plane * nz);
+    const float inv = 1.0f / (float)n1;
+    constexpr int LB = 16;
+    for (int i0 = tid; i0 < N; i0 += LB * 256) {
+      float v[LB];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = i0 + u * 256;
+        v[u] = idx < N ? ld_in(in + idx) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = i0 + u * 256;
+        if (idx < N) {
+          const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
+          A[cmp<FMT>(row, idx - row * n1, kch)] = Op<FMT>::cvt(v[u]);
+        }
+      }
+    }
+  }
+  if (!wait_phase(&tma_bar, 0)) failed = 1;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  const int q = warp & 3, half = warp >> 2;
+
+  for (int m = 0; m < 2; ++m) {
+    const int na = m ? n2 : n1, nb = m ? n1 : n2;   // contracted size, other in-plane size
+    const int L = nb * nz, ntile = rup(L, 128) / 128;
+    const int Kp = rup(na, KSTEP), Np = rup(na, 16);
+    if (tid == 0 && !failed) {
+      issue_product<FMT>(tmem, A, bm + m * bsz, ntile, Kp, Np);
+      commit(&mbar);
+    }
+    if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (failed) break;
+    // m = 0: D[row = i2 + n2 zl][j = a1] -> A[row' = a1 + n1 zl][k = i2]
+    // m = 1: D[row = a1 + n1 zl][j = a2] -> out[zl][a2][a1]
+    const int nkch = rup(n2, KSTEP) / T16;
+    const int nch = (na + 7) / 8, nit = ntile * nch;
+    for (int it0 = half; it0 < nit; it0 += 4) {
+      uint32_t raw[2][8];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int it = it0 + 2 * u;
+        if (it < nit) {
+          const int t = it / nch, j0 = (it - t * nch) * 8;
+          ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), raw[u]);
+        }
+      }
+      ld_wait();
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int it = it0 + 2 * u;
+        if (it >= nit) break;
+        const int t = it / nch, j0 = (it - t * nch) * 8;
+        const int row = t * 128 + q * 32 + lane;
+        if (row >= L) continue;
+        const int zl = row / nb, b = row - zl * nb;
+        if (m == 0) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = j0 + jj;
+            if (j >= na) break;
+            A[cmp<FMT>(j + n1 * zl, b, nkch)] = Op<FMT>::cvt(__uint_as_float(raw[u][jj]));
+          }
+        } else {
+          const long long ob = base + (long long)zl * plane + b;
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = j0 + jj;
+            if (j >= na) break;
+            if (BACK) st_out(s + ob + (long long)j * n1, __uint_as_float(raw[u][jj]));
+            else st_out(scr + ob + (long long)j * n1, __uint_as_float(raw[u][jj]));
+          }
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (failed) {   // one more bounded wait for MMAs in flight before freeing TMEM
+    for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+  }
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+  if (tid == 0 && failed) atomicExch(err, 1);
+}
+
+// Pass B: for 128 consecutive lines (a1 + n1 a2) of one tensor in the FP32
+// scratch, t = U_3^T x along i3, t /= Lambda, x = U_3 t, in place.
+// work[blockIdx.x] = (patch, first line).
+template <int FMT>
+__global__ void __launch_bounds__(256, 2) k_fd_line(const DevPatch *P, const Tab1D *tabs,
+                                                    const float *fpool, const int2 *work,
+                                                    int interior, float *scr,
+                                                    long long rhs_stride, int cap, int bsz,
+                                                    int tcols, const double *gate, int *err,
+                                                    const unsigned char *tcpool) {
+  using T = typename Op<FMT>::T;
+  constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t tma_bar;
+  __shared__ uint32_t tslot;
+  __shared__ int failed;
+  T *A = reinterpret_cast<T *>(smraw);
+  T *bm = A + cap;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double gv = gate ? *gate : 1.0;
+  const int2 w = work[blockIdx.x];
+  const int l = blockIdx.y;
+  const DevPatch pt = P[w.x];
+  if (gv == 0.0) return;   // inactive MINRES iteration
+  const int n1 = interior ? pt.ni[0] : pt.n[0], n2 = interior ? pt.ni[1] : pt.n[1];
+  const int n3 = interior ? pt.ni[2] : pt.n[2];
+  const int LN = n1 * n2, line0 = w.y, nl = min(128, LN - line0);
+  float *X = scr + (interior ? pt.ioff : pt.off) + (long long)l * LN * n3 +
+             (long long)blockIdx.z * rhs_stride + line0;
+
+  if (tid == 0) {
+    failed = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  const uint32_t bbytes = (uint32_t)(rup(n3, 16) * rup(n3, KSTEP) * (int)sizeof(T));
+  if (tid == 0) {
+    const Tab1D &tb = tabs[pt.tab[2]];
+    stage_b(&tma_bar, bm, bsz, tcpool, tb.tcB[FMT == 1][interior][0], bbytes,
+            tb.tcB[FMT == 1][interior][1], bbytes);
+  }
+  {
+    uint4 *zp = reinterpret_cast<uint4 *>(A);
+    const int nzero = cap * (int)sizeof(T) / 16;
+    for (int i = tid; i < nzero; i += 256) zp[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  __syncthreads();
+  const int Kp = rup(n3, KSTEP), Np = rup(n3, 16), kch = Kp / T16;
+  // operand: row = line (128), k = i3.  A warp moves 8 lines x 4 planes per
+  // instruction: 32-byte runs in global memory, one 16-byte unit per row in
+  // shared memory.
+  {
+    const int r8 = lane & 7, k4 = lane >> 3;
+    const int nk4 = (n3 + 3) / 4, nitem = 16 * nk4;
+    constexpr int LB = 8;
+    for (int i0 = warp; i0 < nitem; i0 += 8 * LB) {
+      float v[LB];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int it = i0 + u * 8;
+        const int rg = it % 16, kg = it / 16;
+        const int row = rg * 8 + r8, k = kg * 4 + k4;
+        v[u] = (it < nitem && row < nl && k < n3) ? __ldg(X + (long long)k * LN + row) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int it = i0 + u * 8;
+        const int rg = it % 16, kg = it / 16;
+        const int row = rg * 8 + r8, k = kg * 4 + k4;
+        if (it < nitem && row < nl && k < n3) A[cmp<FMT>(row, k, kch)] = Op<FMT>::cvt(v[u]);
+      }
+    }
+  }
+  if (!wait_phase(&tma_bar, 0)) failed = 1;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tslot;
+  const int q = warp & 3, half = warp >> 2;
+  const int row = q * 32 + lane;
+  // Lambda = c1 D1[a1] + c2 D2[a2] + c3 D3[a3] (+1, times H^{d-2}, for P_A)
+  const float cl = (float)(2.0 * pt.mu + pt.lam), mu = (float)pt.mu, hs = (float)pt.Hs;
+  const float c0 = (l == 0) ? cl : mu, c1 = (l == 1) ? cl : mu, c2 = (l == 2) ? cl : mu;
+  const float *D0 = fpool + (interior ? tabs[pt.tab[0]].Di : tabs[pt.tab[0]].D);
+  const float *D1 = fpool + (interior ? tabs[pt.tab[1]].Di : tabs[pt.tab[1]].D);
+  const float *D2 = fpool + (interior ? tabs[pt.tab[2]].Di : tabs[pt.tab[2]].D);
+  float lab = 0.f;
+  if (row < nl) {
+    const int line = line0 + row, a2 = line / n1, a1 = line - a2 * n1;
+    lab = c0 * D0[a1] + c1 * D1[a2];
+  }
+  const int nch = Np / 8;
+
+  for (int m = 0; m < 2; ++m) {
+    if (tid == 0 && !failed) {
+      issue_product<FMT>(tmem, A, bm + m * bsz, 1, Kp, Np);
+      commit(&mbar);
+    }
+    if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (failed) break;
+    for (int c0i = half; c0i < nch; c0i += 4) {
+      uint32_t raw[2][8];
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (c0i + 2 * u < nch)
+          ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((c0i + 2 * u) * 8), raw[u]);
+      ld_wait();
+      if (row >= nl) continue;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j0 = (c0i + 2 * u) * 8;
+        if (j0 >= Np) break;
+        if (m == 0) {   // scale by Lambda^{-1}, write back as the next operand
+          float x[8];
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = j0 + jj;
+            float lam = lab + c2 * (j < n3 ? D2[j] : 0.f);
+            if (!interior) lam = hs * (lam + 1.f);
+            x[jj] = (j < n3) ? __fdividef(__uint_as_float(raw[u][jj]), lam) : 0.f;
+          }
+          if (j0 < Kp) {
+            if (FMT == 2) {
+              *reinterpret_cast<float4 *>(&A[cmp<FMT>(row, j0, kch)]) = make_float4(x[0], x[1], x[2], x[3]);
+              if (j0 + 4 < Kp)
+                *reinterpret_cast<float4 *>(&A[cmp<FMT>(row, j0 + 4, kch)]) =
+                    make_float4(x[4], x[5], x[6], x[7]);
+            } else {
+              __nv_bfloat162 h[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
+              *reinterpret_cast<uint4 *>(&A[cmp<FMT>(row, j0, kch)]) =
+                  *reinterpret_cast<const uint4 *>(h);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = j0 + jj;
+            if (j < n3) X[(long long)j * LN + row] = __uint_as_float(raw[u][jj]);
+          }
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (failed) {
+    for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+  }
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+  if (tid == 0 && failed) atomicExch(err, 1);
+}
+
+// ------------------------------------------------------------------ host
+namespace {
+
+int tc_cols(int c) {
+  int t = 32;
+  while (t < c) t *= 2;
+  return t;
+}
+
+struct SlabNeed {
+  bool ok;
+  int nz;                              // planes per pass-A/C CTA
+  int cap_p, bsz_p, tcols_p;           // plane kernel
+  int cap_l, bsz_l, tcols_l;           // line kernel
+};
+
+SlabNeed slab_need(const DevPatch &p, int interior, int fmt, int dim) {
+  const int kstep = (fmt == 2) ? 8 : 16, t16 = (fmt == 2) ? 4 : 8;
+  SlabNeed s{};
+  int n[3];
+  for (int d = 0; d < 3; ++d) n[d] = interior ? p.ni[d] : p.n[d];
+  s.ok = dim == 3;
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 1 || rup(n[d], 16) > 256) s.ok = false;
+  if (!s.ok) return s;
+  const int nmax = std::max(n[0], n[1]);
+  s.nz = std::max(1, std::min(n[2], 128 / nmax));
+  int ntile = 1;
+  for (int m = 0; m < 2; ++m) {
+    const int na = m ? n[1] : n[0], nb = m ? n[0] : n[1];
+    const int Lp = rup(nb * s.nz, 128), Kp = rup(na, kstep), Np = rup(na, 16);
+    s.cap_p = std::max(s.cap_p, (Lp / 8) * (Kp / t16) * 9 * t16);
+    s.bsz_p = std::max(s.bsz_p, Np * Kp);
+    ntile = std::max(ntile, Lp / 128);
+    s.tcols_p = std::max(s.tcols_p, tc_cols((Lp / 128) * Np));
+  }
+  if (s.tcols_p > 512 || ntile > 2) s.ok = false;
+  const int Kp3 = rup(n[2], kstep), Np3 = rup(n[2], 16);
+  s.cap_l = 16 * (Kp3 / t16) * 9 * t16;
+  s.bsz_l = Np3 * Kp3;
+  s.tcols_l = tc_cols(Np3);
+  return s;
+}
+
+size_t slab_smem(int cap, int bsz, int tcols, int fmt) {
+  const int esz = (fmt == 2) ? 4 : 2;
+  const size_t smem = (size_t)(rup(cap, 256) + 2 * rup(bsz, 256)) * esz + 1024;
+  const size_t floor_smem = (size_t)228 * 1024 * (size_t)tcols / 512 + 1024;
+  return std::max(smem, floor_smem);
+}
+
+}  // namespace
+
+// Decide which of the given patches the slab path takes (the rest stay with
+// the SIMT kernel) and build the pass work lists.
+afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> &cand,
+                      std::vector<int> &rest, TcSplit &sp, int dyn_max) {
+  std::vector<int4> pw;
+  std::vector<int2> lw;
+  int cap_p = 0, bsz_p = 0, tcols_p = 32, cap_l = 0, bsz_l = 0, tcols_l = 32;
+  for (int k : cand) {
+    const DevPatch &p = c->hp[k];
+    const SlabNeed s = slab_need(p, interior, fmt, c->dim);
+    const int ncp = std::max(cap_p, s.cap_p), nbp = std::max(bsz_p, s.bsz_p);
+    const int ntp = std::max(tcols_p, s.tcols_p);
+    const int ncl = std::max(cap_l, s.cap_l), nbl = std::max(bsz_l, s.bsz_l);
+    const int ntl = std::max(tcols_l, s.tcols_l);
+    if (!s.ok || slab_smem(ncp, nbp, ntp, fmt) > (size_t)dyn_max ||
+        slab_smem(ncl, nbl, ntl, fmt) > (size_t)dyn_max) {
+      rest.push_back(k);
+      continue;
+    }
+    cap_p = ncp; bsz_p = nbp; tcols_p = ntp; cap_l = ncl; bsz_l = nbl; tcols_l = ntl;
+    const int n1 = interior ? p.ni[0] : p.n[0], n2 = interior ? p.ni[1] : p.n[1];
+    const int n3 = interior ? p.ni[2] : p.n[2];
+    for (int z = 0; z < n3; z += s.nz) pw.push_back(make_int4(k, z, std::min(s.nz, n3 - z), 0));
+    for (int ln = 0; ln < n1 * n2; ln += 128) lw.push_back(make_int2(k, ln));
+  }
+  sp.nplane = (int)pw.size();
+  sp.nline = (int)lw.size();
+  sp.cap_p = rup(std::max(cap_p, 256), 256);
+  sp.bsz_p = rup(std::max(bsz_p, 256), 256);
+  sp.tcols_p = tcols_p;
+  sp.cap_l = rup(std::max(cap_l, 256), 256);
+  sp.bsz_l = rup(std::max(bsz_l, 256), 256);
+  sp.tcols_l = tcols_l;
+  sp.smem_p = slab_smem(sp.cap_p, sp.bsz_p, sp.tcols_p, fmt);
+  sp.smem_l = slab_smem(sp.cap_l, sp.bsz_l, sp.tcols_l, fmt);
+  if (sp.nplane) {
+    AFI_TRY(dalloc(c, (void **)&sp.d_plane, pw.size() * sizeof(int4)));
+    AFI_CUDA(cudaMemcpy(sp.d_plane, pw.data(), pw.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    AFI_TRY(dalloc(c, (void **)&sp.d_line, lw.size() * sizeof(int2)));
+    AFI_CUDA(cudaMemcpy(sp.d_line, lw.data(), lw.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  }
+  return AFI_OK;
+}
+
+// Opt the slab kernels into the largest dynamic shared memory the device
+// allows next to their static shared memory; returns that size.
+afi_status slab_prepare(afi_ctx *c, int *dyn_max) {
+  const void *fns[] = {(const void *)k_fd_plane<2, 0>, (const void *)k_fd_plane<2, 1>,
+                       (const void *)k_fd_plane<1, 0>, (const void *)k_fd_plane<1, 1>,
+                       (const void *)k_fd_line<2>, (const void *)k_fd_line<1>};
+  size_t stat = 0;
+  for (const void *f : fns) {
+    cudaFuncAttributes fa;
+    AFI_CUDA(cudaFuncGetAttributes(&fa, f));
+    stat = std::max(stat, fa.sharedSizeBytes);
+  }
+  *dyn_max = c->smem_optin - (int)stat;
+  for (const void *f : fns)
+    AFI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_max));
+  return AFI_OK;
+}
+
+// The three passes over the slab patches, right-hand sides in chunks that
+// fit the FP32 scratch (the context's local-solver scratch slab).
+afi_status slab_run(afi_ctx *c, int interior, int fmt, const TcSplit &sp, const double *r,
+                    double *s, cudaStream_t st, int nrhs) {
+  if (!sp.nplane) return AFI_OK;
+  const long long stride = interior ? c->n_int : c->n_dof;
+  float *scr = reinterpret_cast<float *>(c->fdscratch);
+  const int chunk = (int)std::max(1LL, (2 * c->fdscratch_n) / std::max(1LL, stride));
+  const Tab1D *tabs = c->tabs;
+  const DevPatch *P = c->patches;
+  const int4 *pw = (const int4 *)sp.d_plane;
+  const int2 *lw = (const int2 *)sp.d_line;
+  for (int j = 0; j < nrhs; j += chunk) {
+    const int nb = std::min(chunk, nrhs - j);
+    const double *rj = r + (long long)j * stride;
+    double *sj = s + (long long)j * stride;
+    const dim3 gp(sp.nplane, c->dim, nb), gl(sp.nline, c->dim, nb);
+    if (fmt == 2) {
+      launch(k_fd_plane<2, 0>, gp, 256, sp.smem_p, st, P, tabs, pw, interior, rj, scr, sj, stride,
+             sp.cap_p, sp.bsz_p, sp.tcols_p, c->gate, c->dflag + 1, (const unsigned char *)c->tcpool);
+      launch(k_fd_line<2>, gl, 256, sp.smem_l, st, P, tabs, (const float *)c->fpool, lw, interior, scr,
+             stride, sp.cap_l, sp.bsz_l, sp.tcols_l, c->gate, c->dflag + 1,
+             (const unsigned char *)c->tcpool);
+      launch(k_fd_plane<2, 1>, gp, 256, sp.smem_p, st, P, tabs, pw, interior, rj, scr, sj, stride,
+             sp.cap_p, sp.bsz_p, sp.tcols_p, c->gate, c->dflag + 1, (const unsigned char *)c->tcpool);
+    } else {
+      launch(k_fd_plane<1, 0>, gp, 256, sp.smem_p, st, P, tabs, pw, interior, rj, scr, sj, stride,
+             sp.cap_p, sp.bsz_p, sp.tcols_p, c->gate, c->dflag + 1, (const unsigned char *)c->tcpool);
+      launch(k_fd_line<1>, gl, 256, sp.smem_l, st, P, tabs, (const float *)c->fpool, lw, interior, scr,
+             stride, sp.cap_l, sp.bsz_l, sp.tcols_l, c->gate, c->dflag + 1,
+             (const unsigned char *)c->tcpool);
+      launch(k_fd_plane<1, 1>, gp, 256, sp.smem_p, st, P, tabs, pw, interior, rj, scr, sj, stride,
+             sp.cap_p, sp.bsz_p, sp.tcols_p, c->gate, c->dflag + 1, (const unsigned char *)c->tcpool);
+    }
+    AFI_LAUNCH_CHECK();
+  }
+  return AFI_OK;
+}
+
+}  // namespace afi

@@ -14,117 +14,44 @@
 // epilogue of the third product, and the last epilogue writes FP64 straight
 // to global memory.
 //
-// Operands use the no-swizzle K-major canonical layout of core matrices
-// (8 rows x 16 bytes); one elected thread issues the MMAs (M = 128 lines per
-// tile, N = output modes padded to 16, K in steps of 32 bytes) and commits
-// them to an mbarrier that all threads wait on with a bounded spin.
-#include "common.cuh"
+// Operands use the no-swizzle K-major layout of core matrices (8 rows x 16
+// bytes); one elected thread issues the MMAs (M = 128 lines per tile, N =
+// output modes padded to 16, K in steps of 32 bytes) and commits them to an
+// mbarrier that all threads wait on with a bounded spin.  The tensor operand
+// lives in a single shared-memory buffer that each epilogue overwrites in
+// place, so three to four CTAs share an SM; FP64 <-> FP32 conversions of the
+// input and output run on the integer pipes (f64_to_f32 / f32_to_f64).
+#include "tc.cuh"
 
 #include <algorithm>
 
 namespace afi {
 
-namespace tc {
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
-// offsets, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-// instruction descriptor: FP32 accumulate, A/B format fmt (2 = TF32, 1 = BF16),
-// both K-major, N and M dimensions
-__device__ __forceinline__ uint32_t idesc(int fmt, int M, int N) {
-  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-template <int FMT>
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  if (FMT == 2)
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d), "l"(a),
-                 "l"(b), "r"(id), "r"(acc));
-  else
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d), "l"(a),
-                 "l"(b), "r"(id), "r"(acc));
-}
-
-__device__ __forceinline__ void commit(uint64_t *mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-      smem_u32(mbar)));
-}
-
-// bounded wait for the given phase of an mbarrier; false on timeout
-__device__ __forceinline__ bool wait_phase(uint64_t *mbar, uint32_t phase) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it)
-    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 "selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(done)
-                 : "r"(smem_u32(mbar)), "r"(phase));
-  return done != 0;
-}
-
-__device__ __forceinline__ void ld16(uint32_t taddr, float *v) {
-  uint32_t r[16];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                 "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-                 "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;");
+// Slots of the B operands in shared memory: one per distinct (table, back)
+// pair of the six mode products, packed 4 bits per product (bits 24.. hold
+// the number of slots).
+__host__ __device__ __forceinline__ unsigned b_slots(int t0, int t1, int t2) {
+  const int tab[3] = {t0, t1, t2};
+  unsigned packed = 0;
+  int nslot = 0;
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int m = 0; m < 6; ++m) {
+    int sl = -1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      if (q < m && sl < 0 && q / 3 == m / 3 && tab[q % 3] == tab[m % 3])
+        sl = (int)((packed >> (4 * q)) & 15u);
+    if (sl < 0) sl = nslot++;
+    packed |= (unsigned)sl << (4 * m);
+  }
+  return packed | ((unsigned)nslot << 24);
 }
-
-// mbarrier expecting `bytes` of asynchronous copies (one arrival)
-__device__ __forceinline__ void expect_tx(uint64_t *mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
-               "r"(bytes));
+__host__ __device__ __forceinline__ int bslot(unsigned packed, int m) {
+  return (int)((packed >> (4 * m)) & 15u);
 }
-
-// 1D bulk copy global -> shared (TMA), completion counted on mbar; 16-byte
-// aligned addresses, size a multiple of 16
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-      : "memory");
-}
-
-template <int FMT> struct Op;
-template <> struct Op<2> {   // TF32: FP32 storage, 4 elements per 16 bytes, 8 per MMA
-  using T = float;
-  static constexpr int T16 = 4, KSTEP = 8;
-  static __device__ __forceinline__ T cvt(float x) { return x; }
-};
-template <> struct Op<1> {   // BF16: 8 elements per 16 bytes, 16 per MMA
-  using T = __nv_bfloat16;
-  static constexpr int T16 = 8, KSTEP = 16;
-  static __device__ __forceinline__ T cvt(float x) { return __float2bfloat16(x); }
-};
-
-__host__ __device__ __forceinline__ int rup(int x, int m) { return (x + m - 1) / m * m; }
-
-// element offset of (row, k) in the K-major core-matrix layout with Kp columns
-template <int FMT>
-__device__ __forceinline__ int cm(int row, int k, int Kp) {
-  constexpr int T16 = Op<FMT>::T16;
-  return (((row >> 3) * (Kp / T16) + k / T16) * 8 + (row & 7)) * T16 + (k % T16);
-}
-
-}  // namespace tc
 
 template <int FMT>
-__global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *tabs,
+__global__ void __launch_bounds__(256, 4) k_fd_tc(const DevPatch *P, const Tab1D *tabs,
                                                const float *fpool, int dim, int interior,
                                                const double *r, double *s, int cap, int bsz,
                                                int tcols, const double *gate, int *err,
@@ -133,25 +60,30 @@ __global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *t
   using namespace tc;
   using T = typename Op<FMT>::T;
   constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
-  if (gate && *gate == 0.0) return;
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ __align__(8) uint64_t tma_bar;
   __shared__ uint32_t tslot;
   __shared__ int failed;
-  T *buf[2] = {reinterpret_cast<T *>(smraw), reinterpret_cast<T *>(smraw) + cap};
-  T *bm = reinterpret_cast<T *>(smraw) + 2 * cap;   // 6 B operands, bsz elements each
+  // one operand buffer, rewritten in place by every epilogue (the MMAs that
+  // read it have completed by then), followed by the B operands
+  T *A = reinterpret_cast<T *>(smraw);
+  T *bm = A + cap;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the gate load overlaps the patch-descriptor loads
+  const double gv = gate ? *gate : 1.0;
   const int k = plist[blockIdx.x], l = blockIdx.y;
   const DevPatch pt = P[k];
+  if (gv == 0.0) return;   // inactive MINRES iteration
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = interior ? pt.ni[d] : pt.n[d];
   const int N = n[0] * n[1] * n[2];
   const long long base =
       (interior ? pt.ioff : pt.off) + (long long)l * N + (long long)blockIdx.z * rhs_stride;
+  const unsigned bs = b_slots(pt.tab[0], pt.tab[1], pt.tab[2]);
 
-  // stage the six B operands (prebuilt in the canonical layout) with TMA
-  // bulk copies while the threads zero the operand buffers
+  // stage the B operands (prebuilt in the canonical layout) with TMA bulk
+  // copies while the threads zero the operand buffer
   if (tid == 0) {
     failed = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar)));
@@ -159,25 +91,56 @@ __global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *t
   }
   __syncthreads();
   if (tid == 0) {
-    uint32_t bytes[6], total = 0;
+    // a product copies its B operand when it is the first user of its slot
+    uint32_t total = 0;
+    unsigned first = 0;
+    int seen = 0;
     for (int m = 0; m < 6; ++m) {
+      const int sl = bslot(bs, m);
+      if (seen & (1 << sl)) continue;
+      seen |= 1 << sl;
+      first |= 1u << m;
       const int nd = n[m % 3];
-      bytes[m] = (uint32_t)(rup(nd, 16) * rup(nd, KSTEP) * (int)sizeof(T));
-      total += bytes[m];
+      total += (uint32_t)(rup(nd, 16) * rup(nd, KSTEP) * (int)sizeof(T));
     }
     expect_tx(&tma_bar, total);
     for (int m = 0; m < 6; ++m) {
-      const Tab1D tb = tabs[pt.tab[m % 3]];
-      bulk_g2s(bm + m * bsz, tcpool + tb.tcB[FMT == 1][interior][m >= 3], bytes[m], &tma_bar);
+      if (!(first & (1u << m))) continue;
+      const int nd = n[m % 3];
+      const long long off = tabs[pt.tab[m % 3]].tcB[FMT == 1][interior][m >= 3];
+      bulk_g2s(bm + bslot(bs, m) * bsz, tcpool + off,
+               (uint32_t)(rup(nd, 16) * rup(nd, KSTEP) * (int)sizeof(T)), &tma_bar);
     }
   }
-  for (int i = tid; i < 2 * cap; i += blockDim.x) buf[0][i] = Op<FMT>::cvt(0.f);
-  __syncthreads();
-  // load the tensor as the first operand: line = i2 + n2 i3, k = i1
   {
-    const int Kp = rup(n[0], KSTEP);
-    for (int idx = tid; idx < N; idx += blockDim.x)
-      buf[0][cm<FMT>(idx / n[0], idx % n[0], Kp)] = Op<FMT>::cvt((float)r[base + idx]);
+    uint4 *z = reinterpret_cast<uint4 *>(A);
+    const int nz = cap * (int)sizeof(T) / 16;
+    for (int i = tid; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  __syncthreads();
+  // load the tensor as the first operand: line = i2 + n2 i3, k = i1; the
+  // loads of a batch are all issued before the first shared-memory store
+  {
+    const int kch = rup(n[0], KSTEP) / T16;
+    const float inv = 1.0f / (float)n[0];
+    constexpr int LB = 16;
+    const double *rb = r + base;
+    for (int i0 = tid; i0 < N; i0 += LB * 256) {
+      double v[LB];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = i0 + u * 256;
+        v[u] = idx < N ? __ldg(rb + idx) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int idx = i0 + u * 256;
+        if (idx < N) {
+          const int line = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
+          A[cmp<FMT>(line, idx - line * n[0], kch)] = Op<FMT>::cvt(f64_to_f32(v[u]));
+        }
+      }
+    }
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
@@ -207,47 +170,62 @@ __global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *t
   int na = n[0], nb = n[1], nc = n[2];   // current operand dims, a fastest
   for (int m = 0; m < 6; ++m) {
     const int L = nb * nc, ntile = rup(L, 128) / 128;
-    const int Kp = rup(na, KSTEP), Np = rup(na, 16);
-    T *A = buf[m & 1];
+    const int Kp = rup(na, KSTEP), Np = rup(na, 16), kch = Kp / T16;
     if (tid == 0 && !failed) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t id = idesc(FMT, 128, Np);
-      const uint32_t sbo = (uint32_t)(Kp / T16) * 128u;
-      const uint32_t a0 = smem_u32(A), b0 = smem_u32(bm + m * bsz);
+      const uint32_t sboA = (uint32_t)kch * kLBO, sboB = (uint32_t)kch * 128u;
+      const uint32_t a0 = smem_u32(A), b0 = smem_u32(bm + bslot(bs, m) * bsz);
       for (int t = 0; t < ntile; ++t)
         for (int ks = 0; ks < Kp / KSTEP; ++ks)
-          mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 16 * sbo + ks * 256, 128, sbo),
-                   sdesc(b0 + ks * 256, 128, sbo), id, ks > 0 ? 1u : 0u);
+          mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 16 * sboA + ks * 2 * kLBO, kLBO, sboA),
+                   sdesc(b0 + ks * 256, 128, sboB), id, ks > 0 ? 1u : 0u);
       commit(&mbar);
     }
     if (!wait_phase(&mbar, (uint32_t)(m & 1))) failed = 1;
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     if (failed) break;
-    // epilogue: D[line][j] -> next operand (rotated) or the FP64 output
+    // epilogue: D[line][j] -> next operand (rotated, in place) or the FP64
+    // output; work items are (tile, 8 columns), split between the two warps
+    // that share a TMEM lane quarter
     const int q = warp & 3, half = warp >> 2;
-    const int nnb = nc, nKp = rup(nb, KSTEP);   // next operand: K = nb, lines = nc * na
-    T *An = buf[(m + 1) & 1];
-    for (int t = 0; t < ntile; ++t) {
-      const int line = t * 128 + q * 32 + lane;
-      const int b = line % nb, c = line / nb;
-      for (int j0 = half * 16; j0 < Np; j0 += 32) {
-        float v[16];
-        ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), v);
-        if (line >= L) continue;
+    const int nnb = nc, nkch = rup(nb, KSTEP) / T16;   // next operand: K = nb, lines = nc * na
+    const int nch = (na + 7) / 8, nit = ntile * nch;
+    // items it = half, half + 2, ...: two TMEM loads in flight per wait
+    for (int it0 = half; it0 < nit; it0 += 4) {
+      uint32_t raw[2][8];
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
+      for (int w = 0; w < 2; ++w) {
+        const int it = it0 + 2 * w;
+        if (it < nit) {
+          const int t = it / nch, j0 = (it - t * nch) * 8;
+          ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), raw[w]);
+        }
+      }
+      ld_wait();
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const int it = it0 + 2 * w;
+        if (it >= nit) break;
+        const int t = it / nch, j0 = (it - t * nch) * 8;
+        const int line = t * 128 + q * 32 + lane;
+        if (line >= L) continue;
+        const int c = line / nb, b = line - c * nb;
+        float lb = 0.f;
+        if (m == 2) lb = c0 * Dv[0][b] + (dim == 3 ? c1 * Dv[1][c] : 0.f);
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) {
           const int j = j0 + jj;
-          if (j >= na) continue;
-          float x = v[jj];
+          if (j >= na) break;
+          float x = __uint_as_float(raw[w][jj]);
           if (m == 2) {   // element r~(a1 = b, a2 = c, a3 = j): scale by Lambda^{-1}
-            float lam = c0 * Dv[0][b] + c1 * Dv[1][c] + c2 * Dv[2][j];
-            if (dim != 3) lam = c0 * Dv[0][b] + c1 * Dv[1][c];
+            float lam = (dim == 3) ? lb + c2 * Dv[2][j] : c0 * Dv[0][b] + c1 * Dv[1][c];
             if (!interior) lam = hs * (lam + 1.f);
-            x = x / lam;
+            x = __fdividef(x, lam);
           }
-          if (m == 5) s[base + b + (long long)n[0] * (c + (long long)n[1] * j)] = (double)x;
-          else An[cm<FMT>(c + nnb * j, b, nKp)] = Op<FMT>::cvt(x);
+          if (m == 5) s[base + line + (long long)n[0] * n[1] * j] = f32_to_f64(x);
+          else A[cmp<FMT>(c + nnb * j, b, nkch)] = Op<FMT>::cvt(x);
         }
       }
     }
@@ -268,33 +246,34 @@ __global__ void __launch_bounds__(256) k_fd_tc(const DevPatch *P, const Tab1D *t
   if (tid == 0 && failed) atomicExch(err, 1);
 }
 
-static int g_tc_dyn_max;
+static int g_tc_dyn_max, g_slab_dyn_max;
 
-// Shared memory, B-operand size and TMEM columns the kernel needs for one
-// patch (operand format fmt: 2 = TF32, 1 = BF16).
-struct TcNeed { int cap, bsz, tcols; bool ok; };
+// Shared memory (operand buffer and B slots), B-operand size and TMEM
+// columns the kernel needs for one patch (fmt: 2 = TF32, 1 = BF16).
+struct TcNeed { int cap, bsz, tcols, nslot; bool ok; };
 
 static TcNeed tc_need(const DevPatch &p, int interior, int fmt) {
-  const int kstep = (fmt == 2) ? 8 : 16;
-  TcNeed t{0, 0, 32, true};
+  const int kstep = (fmt == 2) ? 8 : 16, t16 = (fmt == 2) ? 4 : 8;
+  TcNeed t{0, 0, 32, (int)(b_slots(p.tab[0], p.tab[1], p.tab[2]) >> 24), true};
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = interior ? p.ni[d] : p.n[d];
   for (int d = 0; d < 3; ++d) {
     const int na = n[d], nb = n[(d + 1) % 3], nc = n[(d + 2) % 3];
     const int Lp = tc::rup(nb * nc, 128), Kp = tc::rup(na, kstep), Np = tc::rup(na, 16);
-    t.cap = std::max(t.cap, Lp * Kp);
+    t.cap = std::max(t.cap, (Lp / 8) * (Kp / t16) * 9 * t16);   // padded core matrices
     t.bsz = std::max(t.bsz, Np * Kp);
     const int cols = (Lp / 128) * Np;
     while (t.tcols < cols) t.tcols *= 2;
     if (Np > 256) t.ok = false;
   }
   if (t.tcols > 512) t.ok = false;
+  if (n[0] * n[1] * n[2] >= (1 << 20)) t.ok = false;   // exact float index split
   return t;
 }
 
-static size_t tc_smem(int cap, int bsz, int tcols, int fmt) {
+static size_t tc_smem(int cap, int bsz, int tcols, int nslot, int fmt) {
   const int esz = (fmt == 2) ? 4 : 2;
-  size_t smem = (size_t)(2 * tc::rup(cap, 256) + 6 * tc::rup(bsz, 256)) * esz + 1024;
+  size_t smem = (size_t)(tc::rup(cap, 256) + nslot * tc::rup(bsz, 256)) * esz + 1024;
   // at most 512 / tcols CTAs per SM, so tensor-memory allocation never waits long
   const size_t floor_smem = (size_t)228 * 1024 * (size_t)tcols / 512 + 1024;
   return std::max(smem, floor_smem);
@@ -304,35 +283,38 @@ static size_t tc_smem(int cap, int bsz, int tcols, int fmt) {
 // combined launch still fits; the rest go to the SIMT kernel.
 static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
   std::vector<std::pair<size_t, int>> order;
+  const bool force_slab = (c->opt.variant & AFI_VARIANT_FD_SLAB) != 0;
   for (int k = 0; k < c->npatch; ++k) {
     const TcNeed t = tc_need(c->hp[k], interior, fmt);
-    if (t.ok) order.push_back({tc_smem(t.cap, t.bsz, t.tcols, fmt), k});
+    if (t.ok && !force_slab) order.push_back({tc_smem(t.cap, t.bsz, t.tcols, t.nslot, fmt), k});
   }
   std::sort(order.begin(), order.end());
   std::vector<int> tc, simt;
   std::vector<char> in(c->npatch, 0);
-  int cap = 0, bsz = 0, tcols = 32;
+  int cap = 0, bsz = 0, tcols = 32, nslot = 1;
   for (auto &o : order) {
     const TcNeed t = tc_need(c->hp[o.second], interior, fmt);
     const int ncap = std::max(cap, t.cap), nbsz = std::max(bsz, t.bsz), ncols = std::max(tcols, t.tcols);
-    if (tc_smem(ncap, nbsz, ncols, fmt) > (size_t)g_tc_dyn_max) continue;
-    cap = ncap; bsz = nbsz; tcols = ncols;
+    const int nsl = std::max(nslot, t.nslot);
+    if (tc_smem(ncap, nbsz, ncols, nsl, fmt) > (size_t)g_tc_dyn_max) continue;
+    cap = ncap; bsz = nbsz; tcols = ncols; nslot = nsl;
     in[o.second] = 1;
   }
-  int maxN = 1;
+  std::vector<int> big;
   for (int k = 0; k < c->npatch; ++k) {
     if (in[k]) tc.push_back(k);
-    else {
-      simt.push_back(k);
-      maxN = std::max(maxN, interior ? c->hp[k].Ni : c->hp[k].N);
-    }
+    else big.push_back(k);
   }
+  // tensors too large for one CTA: three-pass slab kernels, else SIMT
+  AFI_TRY(slab_build(c, interior, fmt, big, simt, sp, g_slab_dyn_max));
+  int maxN = 1;
+  for (int k : simt) maxN = std::max(maxN, interior ? c->hp[k].Ni : c->hp[k].N);
   sp.ntc = (int)tc.size();
   sp.nsimt = (int)simt.size();
   sp.cap = tc::rup(cap, 256);
   sp.bsz = tc::rup(bsz, 256);
   sp.tcols = tcols;
-  sp.smem = tc_smem(cap, bsz, tcols, fmt);
+  sp.smem = tc_smem(cap, bsz, tcols, nslot, fmt);
   sp.simt_maxN = maxN;
   if (sp.ntc) {
     AFI_TRY(dalloc(c, (void **)&sp.d_tc, tc.size() * sizeof(int)));
@@ -354,7 +336,7 @@ afi_status fd_tc_prepare(afi_ctx *c) {
   g_tc_dyn_max = c->smem_optin - stat;
   AFI_CUDA(cudaFuncSetAttribute(k_fd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_tc_dyn_max));
   AFI_CUDA(cudaFuncSetAttribute(k_fd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_tc_dyn_max));
-  return AFI_OK;
+  return slab_prepare(c, &g_slab_dyn_max);
 }
 
 // Tensor-core FD on the patches that fit, SIMT FP32 FD on the others.  The
@@ -380,6 +362,7 @@ afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaS
              (const unsigned char *)c->tcpool);
     AFI_LAUNCH_CHECK();
   }
+  AFI_TRY(slab_run(c, interior, fmt, sp, r, s, st, nrhs));
   if (sp.nsimt) AFI_TRY(fd_simt_list(c, interior, sp.d_simt, sp.nsimt, sp.simt_maxN, r, s, st, nrhs));
   return AFI_OK;
 }
@@ -389,7 +372,7 @@ afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaS
 __global__ void k_tc_bops(const Tab1D *tabs, int ntab, const double *pool, unsigned char *tcpool) {
   const int t = blockIdx.y, v = blockIdx.z;   // v = bf16 * 4 + interior * 2 + back
   if (t >= ntab) return;
-  const Tab1D T = tabs[t];
+  const Tab1D &T = tabs[t];
   const int bf = v >> 2, in = (v >> 1) & 1, back = v & 1;
   const int n = in ? T.ni : T.n;
   const double *U = pool + (in ? T.Ui : T.U);

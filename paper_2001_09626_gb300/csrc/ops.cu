@@ -217,8 +217,8 @@ __device__ __forceinline__ RigidNZ rigid_nz(int comp, const double *X, int dim) 
   return r;
 }
 
-constexpr int kGtBlocks = 8;    // blocks per patch for the row-list reduction
-constexpr int kRtChunks = 16;   // blocks per (patch, component) for R^T v
+constexpr int kGtBlocks = 4;    // blocks per patch for the row-list reduction
+constexpr int kRtChunks = 4;    // blocks per (patch, component) for R^T v
 
 // Partial sums of (G^T x) over a strided part of the rows touching patch k:
 // part[(k * kGtBlocks + b) * NM + a].  Each entry touches its translation
@@ -234,6 +234,7 @@ __global__ void __launch_bounds__(256) k_Gt_part(const DevPatch *P, const double
   double acc[NM];
 #pragma unroll
   for (int a = 0; a < NM; ++a) acc[a] = 0.0;
+#pragma unroll 4
   for (int e = ptr[k] + b * blockDim.x + threadIdx.x; e < ptr[k + 1]; e += gridDim.x * blockDim.x) {
     int2 en = ent[e];
     double xv = x[en.x >> 1];
@@ -285,6 +286,7 @@ __global__ void __launch_bounds__(256) k_Rt_part(const DevPatch *P, const double
   const double *vc = v + pt.off + (long long)comp * pt.N;
   const double *Xb = ctrl + pt.xoff;
   double acc[3] = {0.0, 0.0, 0.0};
+#pragma unroll 4
   for (int i = ch * blockDim.x + threadIdx.x; i < pt.N; i += gridDim.x * blockDim.x) {
     const double xv = vc[i];
     const RigidNZ r = rigid_nz(comp, Xb + (long long)i * dim, dim);

@@ -499,7 +499,10 @@ void free_context(afi_ctx *c) {
                   c->GtG, c->GtG_inv, c->RtR_inv, c->ws, c->fdscratch, c->small, c->part,
                   c->dflag, c->tcsplit[0][0].d_tc, c->tcsplit[0][0].d_simt, c->tcsplit[0][1].d_tc,
                   c->tcsplit[0][1].d_simt, c->tcsplit[1][0].d_tc, c->tcsplit[1][0].d_simt,
-                  c->tcsplit[1][1].d_tc, c->tcsplit[1][1].d_simt};
+                  c->tcsplit[1][1].d_tc, c->tcsplit[1][1].d_simt, c->tcsplit[0][0].d_plane,
+                  c->tcsplit[0][0].d_line, c->tcsplit[0][1].d_plane, c->tcsplit[0][1].d_line,
+                  c->tcsplit[1][0].d_plane, c->tcsplit[1][0].d_line, c->tcsplit[1][1].d_plane,
+                  c->tcsplit[1][1].d_line};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);

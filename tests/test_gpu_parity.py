@@ -233,3 +233,31 @@ def test_fd_batched_rhs(case, prec):
             assert torch.equal(bi[j], s.fd(Ri[j].contiguous(), interior=True))
     finally:
         s.set_precision("fp64")
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_fd_special_values(case, prec):
+    """The mixed-precision FD converts FP64 <-> FP32 with integer bit
+    operations: zero maps to zero, scaling the input by a power of two
+    scales the output by the same power exactly (exponent handling), and a
+    NaN spreads over its own (patch, component) block only."""
+    _, prob, orc, s = case
+    s.set_precision(prec)
+    try:
+        x = W.torn_random(prob, 17)[0]
+        z = s.fd(T(np.zeros_like(x))).cpu().numpy()
+        assert np.all(z == 0.0)
+        y = s.fd(T(x)).cpu().numpy()
+        for e in (-20, 20):
+            ys = s.fd(T(np.ldexp(x, e))).cpu().numpy()
+            assert np.array_equal(ys, np.ldexp(y, e))
+        k = prob.npatch // 2
+        lo = int(orc.off[k]) + orc.N[k]          # component 1 of patch k
+        hi = lo + orc.N[k]
+        xn = x.copy()
+        xn[lo + orc.N[k] // 3] = np.nan
+        yn = s.fd(T(xn)).cpu().numpy()
+        assert np.all(np.isnan(yn[lo:hi]))
+        assert np.array_equal(yn[:lo], y[:lo]) and np.array_equal(yn[hi:], y[hi:])
+    finally:
+        s.set_precision("fp64")
