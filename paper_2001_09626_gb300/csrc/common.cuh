@@ -153,6 +153,7 @@ struct afi_ctx {
   std::vector<afi::Tab1D> htab;
   int max_N = 0, max_n = 0;
   int smem_optin = 0;                // opt-in dynamic shared memory per block
+  int nsm = 0;                       // streaming multiprocessors of the device
 
   // device data
   afi::DevPatch *patches = nullptr;

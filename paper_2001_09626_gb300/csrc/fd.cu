@@ -323,6 +323,7 @@ afi_status fd_prepare(afi_ctx *c) {
   AFI_CUDA(cudaGetDevice(&dev));
   AFI_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   c->smem_optin = v;
+  AFI_CUDA(cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev));
   // these kernels have no static shared memory: the whole opt-in size is dynamic
   AFI_CUDA(cudaFuncSetAttribute(k_fd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));
   AFI_CUDA(cudaFuncSetAttribute(k_fd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, v));

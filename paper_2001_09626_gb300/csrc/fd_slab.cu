@@ -57,6 +57,26 @@ __device__ __forceinline__ void stage_b(uint64_t *bar, T *bm, int bsz, const uns
   bulk_g2s(bm + bsz, tcpool + off1, bytes1, bar);
 }
 
+// four consecutive inputs (16-byte aligned) as FP32
+__device__ __forceinline__ void ld4(const double *p, float *v) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+  v[0] = f64_to_f32(a.x); v[1] = f64_to_f32(a.y); v[2] = f64_to_f32(b.x); v[3] = f64_to_f32(b.y);
+}
+__device__ __forceinline__ void ld4(const float *p, float *v) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+// four consecutive K entries of one operand row (16-byte / 8-byte aligned)
+template <int FMT> __device__ __forceinline__ void st4(typename Op<FMT>::T *p, const float *v);
+template <> __device__ __forceinline__ void st4<2>(float *p, const float *v) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <> __device__ __forceinline__ void st4<1>(__nv_bfloat16 *p, const float *v) {
+  __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v[0], v[1]), __floats2bfloat162_rn(v[2], v[3])};
+  *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(h);
+}
+
 __device__ __forceinline__ float ld_in(const double *p) { return f64_to_f32(__ldg(p)); }
 __device__ __forceinline__ float ld_in(const float *p) { return __ldg(p); }
 __device__ __forceinline__ void st_out(double *p, float v) { *p = f32_to_f64(v); }
@@ -68,7 +88,7 @@ __device__ __forceinline__ void st_out(float *p, float v) { *p = v; }
 // U_1 then U_2, FP32 in, FP64 out) on nz planes of one (patch, component,
 // right-hand side) tensor.  work[blockIdx.x] = (patch, first plane, nz).
 template <int FMT, int BACK>
-__global__ void __launch_bounds__(256, 2) k_fd_plane(const DevPatch *P, const Tab1D *tabs,
+__global__ void __launch_bounds__(256, 4) k_fd_plane(const DevPatch *P, const Tab1D *tabs,
                                                      const int4 *work, int interior,
                                                      const double *r, float *scr, double *s,
                                                      long long rhs_stride, int cap, int bsz,
@@ -105,11 +125,15 @@ __global__ void __launch_bounds__(256, 2) k_fd_plane(const DevPatch *P, const Ta
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   __syncthreads();
-  if (tid == 0)
-    stage_b(&tma_bar, bm, bsz, tcpool, tabs[pt.tab[0]].tcB[FMT == 1][interior][BACK],
-            (uint32_t)(rup(n1, 16) * rup(n1, KSTEP) * (int)sizeof(T)),
-            tabs[pt.tab[1]].tcB[FMT == 1][interior][BACK],
-            (uint32_t)(rup(n2, 16) * rup(n2, KSTEP) * (int)sizeof(T)));
+  // both products use one B slot when directions 1 and 2 share a table
+  const int slot1 = (pt.tab[0] == pt.tab[1]) ? 0 : 1;
+  if (tid == 0) {
+    const uint32_t b0 = (uint32_t)(rup(n1, 16) * rup(n1, KSTEP) * (int)sizeof(T));
+    const uint32_t b1 = (uint32_t)(rup(n2, 16) * rup(n2, KSTEP) * (int)sizeof(T));
+    expect_tx(&tma_bar, slot1 ? b0 + b1 : b0);
+    bulk_g2s(bm, tcpool + tabs[pt.tab[0]].tcB[FMT == 1][interior][BACK], b0, &tma_bar);
+    if (slot1) bulk_g2s(bm + bsz, tcpool + tabs[pt.tab[1]].tcB[FMT == 1][interior][BACK], b1, &tma_bar);
+  }
   {
     uint4 *zp = reinterpret_cast<uint4 *>(A);
     const int nzero = cap * (int)sizeof(T) / 16;
@@ -117,9 +141,32 @@ __global__ void __launch_bounds__(256, 2) k_fd_plane(const DevPatch *P, const Ta
   }
   __syncthreads();
   // first operand: row = i2 + n2 * zl, k = i1 (the slice is contiguous)
-  {
-    const int kch = rup(n1, KSTEP) / T16, N = (int)(plane * nz);
-    const float inv = 1.0f / (float)n1;
+  const int kch0 = rup(n1, KSTEP) / T16, N = (int)(plane * nz);
+  const float inv = 1.0f / (float)n1;
+  if ((n1 & 3) == 0 && ((uintptr_t)in & 15) == 0) {
+    // four consecutive i1 of one row per thread: 16-byte global loads and
+    // one 16-byte (TF32) or 8-byte (BF16) shared store
+    constexpr int LB = 8;
+    const int N4 = N >> 2;
+    for (int g0 = tid; g0 < N4; g0 += LB * 256) {
+      float v[LB][4];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int g = g0 + u * 256;
+        if (g < N4) ld4(in + 4 * g, v[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int g = g0 + u * 256;
+        if (g < N4) {
+          const int idx = 4 * g;
+          const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
+          st4<FMT>(&A[cmp<FMT>(row, idx - row * n1, kch0)], v[u]);
+        }
+      }
+    }
+  } else {
+    const int kch = kch0;
     constexpr int LB = 16;
     for (int i0 = tid; i0 < N; i0 += LB * 256) {
       float v[LB];
@@ -156,7 +203,7 @@ __global__ void __launch_bounds__(256, 2) k_fd_plane(const DevPatch *P, const Ta
     const int L = nb * nz, ntile = rup(L, 128) / 128;
     const int Kp = rup(na, KSTEP), Np = rup(na, 16);
     if (tid == 0 && !failed) {
-      issue_product<FMT>(tmem, A, bm + m * bsz, ntile, Kp, Np);
+      issue_product<FMT>(tmem, A, bm + (m ? slot1 : 0) * bsz, ntile, Kp, Np);
       commit(&mbar);
     }
     if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
@@ -223,7 +270,7 @@ __global__ void __launch_bounds__(256, 2) k_fd_plane(const DevPatch *P, const Ta
 // scratch, t = U_3^T x along i3, t /= Lambda, x = U_3 t, in place.
 // work[blockIdx.x] = (patch, first line).
 template <int FMT>
-__global__ void __launch_bounds__(256, 2) k_fd_line(const DevPatch *P, const Tab1D *tabs,
+__global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab1D *tabs,
                                                     const float *fpool, const int2 *work,
                                                     int interior, float *scr,
                                                     long long rhs_stride, int cap, int bsz,
@@ -432,9 +479,9 @@ SlabNeed slab_need(const DevPatch &p, int interior, int fmt, int dim) {
   return s;
 }
 
-size_t slab_smem(int cap, int bsz, int tcols, int fmt) {
+size_t slab_smem(int cap, int bsz, int tcols, int fmt, int nslot = 2) {
   const int esz = (fmt == 2) ? 4 : 2;
-  const size_t smem = (size_t)(rup(cap, 256) + 2 * rup(bsz, 256)) * esz + 1024;
+  const size_t smem = (size_t)(rup(cap, 256) + nslot * rup(bsz, 256)) * esz + 1024;
   const size_t floor_smem = (size_t)228 * 1024 * (size_t)tcols / 512 + 1024;
   return std::max(smem, floor_smem);
 }
@@ -447,7 +494,7 @@ afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> 
                       std::vector<int> &rest, TcSplit &sp, int dyn_max) {
   std::vector<int4> pw;
   std::vector<int2> lw;
-  int cap_p = 0, bsz_p = 0, tcols_p = 32, cap_l = 0, bsz_l = 0, tcols_l = 32;
+  int cap_p = 0, bsz_p = 0, tcols_p = 32, cap_l = 0, bsz_l = 0, tcols_l = 32, nslot_p = 1;
   for (int k : cand) {
     const DevPatch &p = c->hp[k];
     const SlabNeed s = slab_need(p, interior, fmt, c->dim);
@@ -455,12 +502,14 @@ afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> 
     const int ntp = std::max(tcols_p, s.tcols_p);
     const int ncl = std::max(cap_l, s.cap_l), nbl = std::max(bsz_l, s.bsz_l);
     const int ntl = std::max(tcols_l, s.tcols_l);
-    if (!s.ok || slab_smem(ncp, nbp, ntp, fmt) > (size_t)dyn_max ||
+    const int nsp = std::max(nslot_p, p.tab[0] == p.tab[1] ? 1 : 2);
+    if (!s.ok || slab_smem(ncp, nbp, ntp, fmt, nsp) > (size_t)dyn_max ||
         slab_smem(ncl, nbl, ntl, fmt) > (size_t)dyn_max) {
       rest.push_back(k);
       continue;
     }
     cap_p = ncp; bsz_p = nbp; tcols_p = ntp; cap_l = ncl; bsz_l = nbl; tcols_l = ntl;
+    nslot_p = nsp;
     const int n1 = interior ? p.ni[0] : p.n[0], n2 = interior ? p.ni[1] : p.n[1];
     const int n3 = interior ? p.ni[2] : p.n[2];
     for (int z = 0; z < n3; z += s.nz) pw.push_back(make_int4(k, z, std::min(s.nz, n3 - z), 0));
@@ -474,7 +523,7 @@ afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> 
   sp.cap_l = rup(std::max(cap_l, 256), 256);
   sp.bsz_l = rup(std::max(bsz_l, 256), 256);
   sp.tcols_l = tcols_l;
-  sp.smem_p = slab_smem(sp.cap_p, sp.bsz_p, sp.tcols_p, fmt);
+  sp.smem_p = slab_smem(sp.cap_p, sp.bsz_p, sp.tcols_p, fmt, nslot_p);
   sp.smem_l = slab_smem(sp.cap_l, sp.bsz_l, sp.tcols_l, fmt);
   if (sp.nplane) {
     AFI_TRY(dalloc(c, (void **)&sp.d_plane, pw.size() * sizeof(int4)));

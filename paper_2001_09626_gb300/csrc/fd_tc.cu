@@ -50,8 +50,8 @@ __host__ __device__ __forceinline__ int bslot(unsigned packed, int m) {
   return (int)((packed >> (4 * m)) & 15u);
 }
 
-template <int FMT>
-__global__ void __launch_bounds__(256, 4) k_fd_tc(const DevPatch *P, const Tab1D *tabs,
+template <int FMT, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, const Tab1D *tabs,
                                                const float *fpool, int dim, int interior,
                                                const double *r, double *s, int cap, int bsz,
                                                int tcols, const double *gate, int *err,
@@ -125,16 +125,16 @@ __global__ void __launch_bounds__(256, 4) k_fd_tc(const DevPatch *P, const Tab1D
     const float inv = 1.0f / (float)n[0];
     constexpr int LB = 16;
     const double *rb = r + base;
-    for (int i0 = tid; i0 < N; i0 += LB * 256) {
+    for (int i0 = tid; i0 < N; i0 += LB * NT) {
       double v[LB];
 #pragma unroll
       for (int u = 0; u < LB; ++u) {
-        const int idx = i0 + u * 256;
+        const int idx = i0 + u * NT;
         v[u] = idx < N ? __ldg(rb + idx) : 0.0;
       }
 #pragma unroll
       for (int u = 0; u < LB; ++u) {
-        const int idx = i0 + u * 256;
+        const int idx = i0 + u * NT;
         if (idx < N) {
           const int line = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
           A[cmp<FMT>(line, idx - line * n[0], kch)] = Op<FMT>::cvt(f64_to_f32(v[u]));
@@ -187,17 +187,18 @@ __global__ void __launch_bounds__(256, 4) k_fd_tc(const DevPatch *P, const Tab1D
     __syncthreads();
     if (failed) break;
     // epilogue: D[line][j] -> next operand (rotated, in place) or the FP64
-    // output; work items are (tile, 8 columns), split between the two warps
-    // that share a TMEM lane quarter
+    // output; work items are (tile, 8 columns), split between the NT / 128
+    // warps that share a TMEM lane quarter
+    constexpr int G = NT / 128;
     const int q = warp & 3, half = warp >> 2;
     const int nnb = nc, nkch = rup(nb, KSTEP) / T16;   // next operand: K = nb, lines = nc * na
     const int nch = (na + 7) / 8, nit = ntile * nch;
-    // items it = half, half + 2, ...: two TMEM loads in flight per wait
-    for (int it0 = half; it0 < nit; it0 += 4) {
+    // items it = half, half + G, ...: two TMEM loads in flight per wait
+    for (int it0 = half; it0 < nit; it0 += 2 * G) {
       uint32_t raw[2][8];
 #pragma unroll
       for (int w = 0; w < 2; ++w) {
-        const int it = it0 + 2 * w;
+        const int it = it0 + G * w;
         if (it < nit) {
           const int t = it / nch, j0 = (it - t * nch) * 8;
           ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), raw[w]);
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(256, 4) k_fd_tc(const DevPatch *P, const Tab1D
       ld_wait();
 #pragma unroll
       for (int w = 0; w < 2; ++w) {
-        const int it = it0 + 2 * w;
+        const int it = it0 + G * w;
         if (it >= nit) break;
         const int t = it / nch, j0 = (it - t * nch) * 8;
         const int line = t * 128 + q * 32 + lane;
@@ -329,13 +330,17 @@ static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
 }
 
 afi_status fd_tc_prepare(afi_ctx *c) {
-  cudaFuncAttributes fa2, fa1;
-  AFI_CUDA(cudaFuncGetAttributes(&fa2, k_fd_tc<2>));
-  AFI_CUDA(cudaFuncGetAttributes(&fa1, k_fd_tc<1>));
-  const int stat = (int)std::max(fa2.sharedSizeBytes, fa1.sharedSizeBytes);
-  g_tc_dyn_max = c->smem_optin - stat;
-  AFI_CUDA(cudaFuncSetAttribute(k_fd_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_tc_dyn_max));
-  AFI_CUDA(cudaFuncSetAttribute(k_fd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, g_tc_dyn_max));
+  const void *fns[] = {(const void *)k_fd_tc<2, 256>, (const void *)k_fd_tc<2, 512>,
+                       (const void *)k_fd_tc<1, 256>, (const void *)k_fd_tc<1, 512>};
+  size_t stat = 0;
+  for (const void *f : fns) {
+    cudaFuncAttributes fa;
+    AFI_CUDA(cudaFuncGetAttributes(&fa, f));
+    stat = std::max(stat, fa.sharedSizeBytes);
+  }
+  g_tc_dyn_max = c->smem_optin - (int)stat;
+  for (const void *f : fns)
+    AFI_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, g_tc_dyn_max));
   return slab_prepare(c, &g_slab_dyn_max);
 }
 
@@ -350,16 +355,21 @@ afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaS
   const long long stride = interior ? c->n_int : c->n_dof;
   if (sp.ntc) {
     const dim3 grid(sp.ntc, c->dim, nrhs);
-    if (fmt == 2)
-      launch(k_fd_tc<2>, grid, 256, sp.smem, st, (const DevPatch *)c->patches,
-             (const Tab1D *)c->tabs, (const float *)c->fpool, c->dim, interior, r, s, sp.cap,
-             sp.bsz, sp.tcols, c->gate, c->dflag + 1, stride, (const int *)sp.d_tc,
-             (const unsigned char *)c->tcpool);
-    else
-      launch(k_fd_tc<1>, grid, 256, sp.smem, st, (const DevPatch *)c->patches,
-             (const Tab1D *)c->tabs, (const float *)c->fpool, c->dim, interior, r, s, sp.cap,
-             sp.bsz, sp.tcols, c->gate, c->dflag + 1, stride, (const int *)sp.d_tc,
-             (const unsigned char *)c->tcpool);
+    // a grid that fills the SMs at most twice: 512 threads per tensor to
+    // shorten each CTA's chain of mode products; else 256 (more CTAs per SM)
+    const bool wide = (long long)sp.ntc * c->dim * nrhs <= 2LL * c->nsm;
+    auto args = [&](auto kern, int nt) {
+      launch(kern, grid, nt, sp.smem, st, (const DevPatch *)c->patches, (const Tab1D *)c->tabs,
+             (const float *)c->fpool, c->dim, interior, r, s, sp.cap, sp.bsz, sp.tcols, c->gate,
+             c->dflag + 1, stride, (const int *)sp.d_tc, (const unsigned char *)c->tcpool);
+    };
+    if (fmt == 2) {
+      if (wide) args(k_fd_tc<2, 512>, 512);
+      else args(k_fd_tc<2, 256>, 256);
+    } else {
+      if (wide) args(k_fd_tc<1, 512>, 512);
+      else args(k_fd_tc<1, 256>, 256);
+    }
     AFI_LAUNCH_CHECK();
   }
   AFI_TRY(slab_run(c, interior, fmt, sp, r, s, st, nrhs));
