@@ -214,6 +214,8 @@ def config(name: str, seed: int = 0) -> Problem:
     # oracle-sized variants of the same geometry kinds
     if name == "C2-small":
         return unit_box(3, (2, 2, 2), 3, 4, jitter=0.1, seed=seed, name=name)
+    if name == "C2-quarter":   # C2 patches (p=3, 16^3 elements), 2x2x3 of them
+        return unit_box(3, (2, 2, 3), 3, 16, jitter=0.1, seed=seed, name=name)
     if name == "C2-mid":
         return unit_box(3, (3, 3, 3), 3, 6, jitter=0.1, seed=seed, name=name)
     if name == "C4-small":

@@ -4,8 +4,8 @@
 //    univariate stiffness / mass matrices K_hat, M_hat (Section 5.2);
 //  * the generalised eigendecomposition U^T K U = D, U^T M U = I of eq. (5.8)
 //    by Cholesky reduction plus parallel cyclic Jacobi;
-//  * Cholesky factorisation and explicit inverse of G^T G (eq. 4.6) and of
-//    the per-patch R^T R (projection P_u).
+//  * explicit inverses of G^T G (eq. 4.6, Gauss-Jordan over the whole grid)
+//    and of the per-patch R^T R (projection P_u).
 #include "common.cuh"
 
 #include <cmath>
@@ -388,52 +388,33 @@ __global__ void k_to_low(const double *src, float *f, __nv_bfloat16 *b, long lon
   b[i] = __double2bfloat16(src[i]);
 }
 
-// ------------------------------------------------ Cholesky and inverses
-// In-place Cholesky of an SPD n x n matrix (lower), one block.
-__global__ void k_chol(double *A, int n, int *flag) {
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      double d = A[(long long)j * n + j];
-      if (!(d > 0.0)) { bad = 1; d = 1.0; }
-      A[(long long)j * n + j] = sqrt(d);
-    }
-    __syncthreads();
-    double d = A[(long long)j * n + j];
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(long long)i * n + j] /= d;
-    __syncthreads();
-    long long m = n - j - 1;
-    for (long long idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      int i = j + 1 + (int)(idx / m), k = j + 1 + (int)(idx % m);
-      if (k <= i) A[(long long)i * n + k] -= A[(long long)i * n + j] * A[(long long)k * n + j];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0 && bad) atomicExch(flag, 1);
+// ---------------------------------------------------- dense SPD inverse
+// Gauss-Jordan elimination without pivoting (the pivots of an SPD matrix
+// are the diagonals of its successive Schur complements, all positive), one
+// grid-wide launch per pivot k, ping-pong src -> dst:
+//   row k:    dst[k][j] = src[k][j] / src[k][k]   (and 1 / src[k][k] at j = k)
+//   row i!=k: dst[i][j] = src[i][j] - src[i][k] dst[k][j]   (0 - ... at j = k)
+// After the n steps the buffer holds A^{-1}.  pinv[k] = 1 / pivot k is
+// written by the thread that computes that diagonal entry one step earlier,
+// so each step divides once.
+__global__ void k_gj_first(const double *A, double *pinv, int *flag) {
+  const double d = A[0];
+  if (!(d > 0.0) || !isfinite(d)) { atomicExch(flag, 1); pinv[0] = 0.0; }
+  else pinv[0] = 1.0 / d;
 }
 
-// Linv column j = L^{-1} e_j (forward substitution), one thread per column.
-__global__ void k_trinv(const double *L, double *Linv, int n) {
-  int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= n) return;
-  for (int i = 0; i < n; ++i) {
-    double s = (i == col) ? 1.0 : 0.0;
-    if (i > col)
-      for (int k = col; k < i; ++k) s -= L[(long long)i * n + k] * Linv[(long long)k * n + col];
-    Linv[(long long)i * n + col] = (i < col) ? 0.0 : s / L[(long long)i * n + i];
+__global__ void k_gj_step(const double *src, double *dst, int n, int k, double *pinv, int *flag) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (j >= n) return;
+  const double p = pinv[k];
+  const long long at = (long long)i * n + j;
+  const double rk = (j == k) ? p : src[(long long)k * n + j] * p;
+  const double v = (i == k) ? rk : ((j == k) ? 0.0 : src[at]) - src[(long long)i * n + k] * rk;
+  dst[at] = v;
+  if (i == k + 1 && j == k + 1) {
+    if (!(v > 0.0) || !isfinite(v)) { atomicExch(flag, 1); pinv[k + 1] = 0.0; }
+    else pinv[k + 1] = 1.0 / v;
   }
-}
-
-// Ainv = Linv^T Linv.
-__global__ void k_ltl(const double *Linv, double *Ainv, int n) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * n) return;
-  int i = (int)(idx / n), j = (int)(idx % n);
-  double s = 0.0;
-  for (int k = max(i, j); k < n; ++k) s += Linv[(long long)k * n + i] * Linv[(long long)k * n + j];
-  Ainv[idx] = s;
 }
 
 // Per patch nm x nm SPD inverse by Gauss-Jordan (one thread per patch).
@@ -494,14 +475,19 @@ afi_status build_1d_tables(afi_ctx *c) {
   return AFI_OK;
 }
 
+// Ainv = A^{-1} for SPD A (n x n); scratch holds n*n + n doubles.  A is
+// left unchanged.
 afi_status dense_spd_inverse(afi_ctx *c, double *A, double *Ainv, int n, double *scratch) {
-  launch(k_chol, 1, 1024, 0, 0, A, n, c->dflag);
+  double *buf[2] = {Ainv, scratch};
+  double *pinv = scratch + (long long)n * n;
+  AFI_CUDA(cudaMemcpy(Ainv, A, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice));
+  launch(k_gj_first, 1, 1, 0, 0, (const double *)Ainv, pinv, c->dflag);
+  const dim3 grid((n + 255) / 256, n);
+  for (int k = 0; k < n; ++k)
+    launch(k_gj_step, grid, 256, 0, 0, (const double *)buf[k & 1], buf[(k + 1) & 1], n, k, pinv, c->dflag);
   AFI_LAUNCH_CHECK();
-  launch(k_trinv, (n + 127) / 128, 128, 0, 0, A, scratch, n);
-  AFI_LAUNCH_CHECK();
-  long long nn = (long long)n * n;
-  launch(k_ltl, (unsigned)((nn + 255) / 256), 256, 0, 0, scratch, Ainv, n);
-  AFI_LAUNCH_CHECK();
+  if (n & 1)
+    AFI_CUDA(cudaMemcpy(Ainv, scratch, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice));
   int h = 0;
   AFI_CUDA(cudaMemcpy(&h, c->dflag, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) { set_error("G^T G is not positive definite (too few constraints?)"); return AFI_ESINGULAR; }

@@ -137,7 +137,8 @@ afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s) 
 }
 
 // ------------------------------------------------------------------ jumps
-__global__ void k_B(const int2 *rc, long n_c, const double *x, double *y, double alpha, int acc) {
+__global__ void k_B(const int2 *rc, long n_c, const double *x, double *y, double alpha, int acc, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= n_c) return;
   int2 e = rc[r];
@@ -146,7 +147,8 @@ __global__ void k_B(const int2 *rc, long n_c, const double *x, double *y, double
 }
 
 __global__ void k_Bt(const int *shell, const int *ptr, const int *ent, long ns, const double *x,
-                     double *y, double alpha, int acc) {
+                     double *y, double alpha, int acc, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   long s = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (s >= ns) return;
   double v = 0.0;
@@ -159,7 +161,8 @@ __global__ void k_Bt(const int *shell, const int *ptr, const int *ent, long ns, 
   y[dof] = acc ? y[dof] + alpha * v : alpha * v;
 }
 
-__global__ void k_BBt_inv(const int2 *grp, long n_c, const double *x, double *y) {
+__global__ void k_BBt_inv(const int2 *grp, long n_c, const double *x, double *y, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= n_c) return;
   int2 g = grp[r];
@@ -169,9 +172,50 @@ __global__ void k_BBt_inv(const int2 *grp, long n_c, const double *x, double *y)
   y[r] = x[r] - s / (double)g.y;
 }
 
+// y = B^T (B B^T)^{-1} x over the shell dofs (other entries of y untouched).
+// The rows touching one dof all belong to its node's group, whose block of
+// B B^T is inverted in closed form (I - 1 1^T / m for a star of m copies).
+__global__ void k_Bt_inv(const int *shell, const int *ptr, const int *ent, const int2 *grp, long ns,
+                         const double *x, double *y, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
+  long s = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const int e0 = ptr[s], e1 = ptr[s + 1];
+  const int2 g = grp[ent[e0] >> 1];
+  double corr = 0.0;
+  if (g.y > 0) {
+    double sum = 0.0;
+    for (int j = 0; j < g.y - 1; ++j) sum += x[g.x + j];
+    corr = sum / (double)g.y;
+  }
+  double v = 0.0;
+  for (int e = e0; e < e1; ++e) {
+    const int code = ent[e];
+    const double xv = x[code >> 1] - corr;
+    v += (code & 1) ? -xv : xv;
+  }
+  y[shell[s]] = v;
+}
+
+// y = (B B^T)^{-1} B x: each row recomputes the jumps of its group's rows.
+__global__ void k_B_inv(const int2 *rc, const int2 *grp, long n_c, const double *x, double *y, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
+  long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= n_c) return;
+  const int2 e = rc[r], g = grp[r];
+  const double own = x[e.x] - (e.y >= 0 ? x[e.y] : 0.0);
+  if (g.y == 0) { y[r] = own; return; }
+  double sum = 0.0;
+  for (int j = 0; j < g.y - 1; ++j) {
+    const int2 f = rc[g.x + j];
+    sum += x[f.x] - (f.y >= 0 ? x[f.y] : 0.0);
+  }
+  y[r] = own - sum / (double)g.y;
+}
+
 afi_status op_B(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->n_c == 0) return AFI_OK;
-  launch(k_B, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->row_copy, c->n_c, x, y, 1.0, 0);
+  launch(k_B, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->row_copy, c->n_c, x, y, 1.0, 0, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -181,7 +225,7 @@ static afi_status op_Bt_scaled(afi_ctx *c, const double *x, double *y, double al
   if (zero_first) AFI_CUDA(cudaMemsetAsync(y, 0, c->n_dof * sizeof(double), s));
   if (c->n_shell == 0) return AFI_OK;
   launch(k_Bt, (unsigned)((c->n_shell + 255) / 256), 256, 0, s, c->shell_dof, c->bt_ptr, c->bt_ent,
-                                                            c->n_shell, x, y, alpha, acc ? 1 : 0);
+                                                            c->n_shell, x, y, alpha, acc ? 1 : 0, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -193,7 +237,7 @@ afi_status op_Bt(afi_ctx *c, const double *x, double *y, bool accumulate, bool z
 
 afi_status op_BBt_inv(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->n_c == 0) return AFI_OK;
-  launch(k_BBt_inv, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->row_grp, c->n_c, x, y);
+  launch(k_BBt_inv, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->row_grp, c->n_c, x, y, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -217,8 +261,26 @@ __device__ __forceinline__ RigidNZ rigid_nz(int comp, const double *X, int dim) 
   return r;
 }
 
+constexpr int kCounters = 3072;  // block tickets of the last-block reductions, in c->small
 constexpr int kGtBlocks = 4;    // blocks per patch for the row-list reduction
 constexpr int kRtChunks = 4;    // blocks per (patch, component) for R^T v
+
+// After each block has written its partials: true (in every thread) in the
+// block that finishes last, which then combines all partials; it resets the
+// ticket counter for the next launch.
+__device__ __forceinline__ bool last_block(unsigned *counter) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+    last = atomicAdd(counter, 1u) == nb - 1;
+    if (last) *counter = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
 
 // Partial sums of (G^T x) over a strided part of the rows touching patch k:
 // part[(k * kGtBlocks + b) * NM + a].  Each entry touches its translation
@@ -227,7 +289,9 @@ constexpr int kRtChunks = 4;    // blocks per (patch, component) for R^T v
 template <int NM>
 __global__ void __launch_bounds__(256) k_Gt_part(const DevPatch *P, const double *ctrl,
                                                  const int *ptr, const int2 *ent, const double *x,
-                                                 double *part, int dim) {
+                                                 double *part, int dim, unsigned *counter,
+                                                 double *g, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   __shared__ double sh[8 * NM];
   const int k = blockIdx.y, b = blockIdx.x;
   const DevPatch pt = P[k];
@@ -253,33 +317,25 @@ __global__ void __launch_bounds__(256) k_Gt_part(const DevPatch *P, const double
   block_sum_multi<256>(acc, NM, sh);
   if (threadIdx.x == 0)
     for (int a = 0; a < NM; ++a) part[((long long)k * gridDim.x + b) * NM + a] = acc[a];
-}
-
-// g[k][a] = sum over the nb partial blocks (fixed order); optionally y = Minv_k g_k.
-__global__ void k_part_final(const double *part, int nb, int nm, int npatch, double *g,
-                             const double *Minv) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= npatch) return;
-  double t[6];
-  for (int a = 0; a < nm; ++a) {
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[((long long)k * nb + b) * nm + a];
-    t[a] = s;
-  }
-  for (int a = 0; a < nm; ++a) {
-    double v = t[a];
-    if (Minv) {
-      v = 0.0;
-      for (int b = 0; b < nm; ++b) v += Minv[((long long)k * nm + a) * nm + b] * t[b];
-    }
-    g[k * nm + a] = v;
+  // g[k][a] = sum over the blocks of patch k, in block order
+  if (!last_block(counter)) return;
+  const int npatch = gridDim.y;
+  const volatile double *vp = part;
+  for (int e = threadIdx.x; e < npatch * NM; e += blockDim.x) {
+    const int kk = e / NM, a = e - kk * NM;
+    double sum = 0.0;
+    for (int bb = 0; bb < (int)gridDim.x; ++bb) sum += vp[((long long)kk * gridDim.x + bb) * NM + a];
+    g[e] = sum;
   }
 }
 
 // Partial sums of R_k^T v over one chunk of one component block: the
 // translation and the two rotation products, part[((k*dim + comp)*CH + ch)*3].
 __global__ void __launch_bounds__(256) k_Rt_part(const DevPatch *P, const double *ctrl,
-                                                 const double *v, double *part, int dim) {
+                                                 const double *v, double *part, int dim,
+                                                 unsigned *counter, int nm, double *g,
+                                                 const double *Minv, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   __shared__ double sh[8 * 3];
   const int ch = blockIdx.x, comp = blockIdx.y, k = blockIdx.z;
   const DevPatch pt = P[k];
@@ -297,43 +353,38 @@ __global__ void __launch_bounds__(256) k_Rt_part(const DevPatch *P, const double
   block_sum_multi<256>(acc, 3, sh);
   if (threadIdx.x == 0)
     for (int a = 0; a < 3; ++a) part[(((long long)k * dim + comp) * gridDim.x + ch) * 3 + a] = acc[a];
-}
-
-// g[k][a] from the R^T v partials, optionally y = Minv_k g_k.  One warp per
-// patch: lanes sum the chunks of each (component, product) in a fixed order.
-__global__ void k_Rt_final(const double *part, int nch, int dim, int nm, int npatch, double *g,
-                           const double *Minv) {
-  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (k >= npatch) return;
-  double t[6] = {0, 0, 0, 0, 0, 0};
-  const double X0[3] = {0.0, 0.0, 0.0};
-  for (int comp = 0; comp < dim; ++comp) {
-    const RigidNZ r = rigid_nz(comp, X0, dim);   // only the mode indices are used
-    double q[3] = {0.0, 0.0, 0.0};
-    for (int ch = lane; ch < nch; ch += 32)
-      for (int a = 0; a < 3; ++a) q[a] += part[(((long long)k * dim + comp) * nch + ch) * 3 + a];
-    for (int a = 0; a < 3; ++a)
-      for (int o = 16; o > 0; o >>= 1) q[a] += __shfl_xor_sync(0xffffffffu, q[a], o);
-    t[comp] += q[0];
-    t[r.m1] += q[1];
-    if (dim == 3) t[r.m2] += q[2];
-  }
-  if (lane < nm) {
-    double v;
-    if (Minv) {
-      v = 0.0;
-      for (int b = 0; b < nm; ++b) v += Minv[((long long)k * nm + lane) * nm + b] * t[b];
-    } else {
-      v = (lane == 0) ? t[0] : (lane == 1) ? t[1] : (lane == 2) ? t[2] : (lane == 3) ? t[3]
-          : (lane == 4) ? t[4] : t[5];
+  // per patch: the modes' sums over components and chunks (fixed order),
+  // then optionally Minv_k times them
+  if (!last_block(counter)) return;
+  const volatile double *vp = part;
+  const int nch = gridDim.x;
+  for (int kk = threadIdx.x; kk < (int)gridDim.z; kk += blockDim.x) {
+    double t[6] = {0, 0, 0, 0, 0, 0};
+    const double X0[3] = {0.0, 0.0, 0.0};
+    for (int cp = 0; cp < dim; ++cp) {
+      const RigidNZ r = rigid_nz(cp, X0, dim);   // only the mode indices are used
+      double q[3] = {0.0, 0.0, 0.0};
+      for (int c2 = 0; c2 < nch; ++c2)
+        for (int a = 0; a < 3; ++a) q[a] += vp[(((long long)kk * dim + cp) * nch + c2) * 3 + a];
+      t[cp] += q[0];
+      t[r.m1] += q[1];
+      if (dim == 3) t[r.m2] += q[2];
     }
-    g[k * nm + lane] = v;
+    for (int a = 0; a < nm; ++a) {
+      double val = t[a];
+      if (Minv) {
+        val = 0.0;
+        for (int b2 = 0; b2 < nm; ++b2) val += Minv[((long long)kk * nm + a) * nm + b2] * t[b2];
+      }
+      g[kk * nm + a] = val;
+    }
   }
 }
 
 // dst = src - R_k y_k on every dof (y per patch, NM entries).
 __global__ void k_Rsub(const DevPatch *P, const double *ctrl, const double *src, double *dst,
-                       const double *y, int dim, int nm) {
+                       const double *y, int dim, int nm, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   const int comp = blockIdx.y, k = blockIdx.z;
   const DevPatch pt = P[k];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -347,7 +398,8 @@ __global__ void k_Rsub(const DevPatch *P, const double *ctrl, const double *src,
 }
 
 // dense y = M g (M: n x n), one warp per row.
-__global__ void k_dense_mv(const double *M, const double *g, double *y, int n) {
+__global__ void k_dense_mv(const double *M, const double *g, double *y, int n, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (row >= n) return;
   double s = 0.0;
@@ -366,7 +418,8 @@ __device__ __forceinline__ double rigid_apply(int comp, const double *X, const d
 
 // out[r] (= or -=) sum over the row's copies of sign * (R_k y_k)(copy).
 __global__ void k_G(const DevPatch *P, const double *ctrl, const int2 *rc, const int2 *rk, long n_c,
-                    const double *y, double *out, int dim, int nm, int subtract, const double *src) {
+                    const double *y, double *out, int dim, int nm, int subtract, const double *src, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= n_c) return;
   int2 e = rc[r], kk = rk[r];
@@ -388,19 +441,20 @@ __global__ void k_G(const DevPatch *P, const double *ctrl, const int2 *rc, const
 
 afi_status op_Gt_rows(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
   dim3 gr(kGtBlocks, c->npatch);
-  if (c->nm == 6) launch(k_Gt_part<6>, gr, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, c->part, c->dim);
-  else launch(k_Gt_part<3>, gr, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, c->part, c->dim);
-  launch(k_part_final, (c->npatch + 127) / 128, 128, 0, s, (const double *)c->part, kGtBlocks, c->nm,
-         c->npatch, g, (const double *)nullptr);
+  unsigned *cnt = reinterpret_cast<unsigned *>(c->small + kCounters) + 2;
+  if (c->nm == 6)
+    launch(k_Gt_part<6>, gr, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, c->part, c->dim, cnt, g, (const double *)c->gate);
+  else
+    launch(k_Gt_part<3>, gr, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, c->part, c->dim, cnt, g, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 // g = R^T v per patch; with Minv, g = Minv_k (R_k^T v) instead.
 static afi_status Rt_apply(afi_ctx *c, const double *x, double *g, const double *Minv, cudaStream_t s) {
-  launch(k_Rt_part, dim3(kRtChunks, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x, c->part, c->dim);
-  launch(k_Rt_final, (c->npatch * 32 + 127) / 128, 128, 0, s, (const double *)c->part, kRtChunks,
-         c->dim, c->nm, c->npatch, g, Minv);
+  unsigned *cnt = reinterpret_cast<unsigned *>(c->small + kCounters) + 3;
+  launch(k_Rt_part, dim3(kRtChunks, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x, c->part,
+         c->dim, cnt, c->nm, g, Minv, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -410,7 +464,7 @@ afi_status op_Rt(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
 }
 
 afi_status op_dense_inv(afi_ctx *c, const double *g, double *y, cudaStream_t s) {
-  launch(k_dense_mv, (c->ng * 32 + 255) / 256, 256, 0, s, c->GtG_inv, g, y, c->ng);
+  launch(k_dense_mv, (c->ng * 32 + 255) / 256, 256, 0, s, c->GtG_inv, g, y, c->ng, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -431,7 +485,7 @@ afi_status op_Pchi(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
 static afi_status G_apply(afi_ctx *c, const double *y, double *out, const double *src, cudaStream_t s) {
   launch(k_G, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->patches, c->ctrl, c->row_copy,
                                                        c->row_patch, c->n_c, y, out, c->dim,
-                                                       c->nm, src ? 1 : 0, src);
+                                                       c->nm, src ? 1 : 0, src, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -445,14 +499,14 @@ afi_status op_Pu(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   double *g = gbuf(c, 0);
   AFI_TRY(Rt_apply(c, x, g, c->RtR_inv, s));
   launch(k_Rsub, dim3((c->max_N + 255) / 256, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x,
-         y, (const double *)g, c->dim, c->nm);
+         y, (const double *)g, c->dim, c->nm, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 afi_status op_R_sub(afi_ctx *c, const double *y, double *v, cudaStream_t s) {
   launch(k_Rsub, dim3((c->max_N + 255) / 256, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl,
-         (const double *)v, v, y, c->dim, c->nm);
+         (const double *)v, v, y, c->dim, c->nm, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -498,12 +552,16 @@ afi_status dot(afi_ctx *c, const double *a, const double *b, long n, double *dst
 // ------------------------------------------------- composite operators
 afi_status op_PS(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   // (B B^T)^{-1} B [blkdiag H^{d-2} S_hat] B^T (B B^T)^{-1} x  (Remark 1)
-  double *t1 = c->ws, *t2 = c->ws + c->n_dof, *m1 = c->ws + 2 * c->n_dof;
-  AFI_TRY(op_BBt_inv(c, x, m1, s));
-  AFI_TRY(op_Bt(c, m1, t1, false, false, s));
+  double *t1 = c->ws, *t2 = c->ws + c->n_dof;
+  if (c->n_c == 0) return AFI_OK;
+  if (c->n_shell)
+    launch(k_Bt_inv, (unsigned)((c->n_shell + 255) / 256), 256, 0, s, (const int *)c->shell_dof,
+           (const int *)c->bt_ptr, (const int *)c->bt_ent, (const int2 *)c->row_grp, c->n_shell, x, t1, (const double *)c->gate);
   AFI_TRY(schur_run(c, t1, t2, s));
-  AFI_TRY(op_B(c, t2, m1, s));
-  return op_BBt_inv(c, m1, y, s);
+  launch(k_B_inv, (unsigned)((c->n_c + 255) / 256), 256, 0, s, (const int2 *)c->row_copy,
+         (const int2 *)c->row_grp, c->n_c, (const double *)t2, y, (const double *)c->gate);
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
 }
 
 afi_status op_precond(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
@@ -576,27 +634,48 @@ __global__ void k_iter_begin(double *st) {
 
 __global__ void k_set(double *st, int idx, double v) { st[idx] = v; }
 
+// v = y / beta_1 before the first iteration
 __global__ void k_v_from_y(const double *y, double *v, long n, const double *st) {
-  if (st[S_ACTIVE] == 0.0) return;
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   v[i] = y[i] * st[S_INVBETA];
 }
 
-__device__ __forceinline__ void block_partial(double s, double *part) {
+// Block partial of a grid-wide sum; the last block to finish (ticket on
+// *counter) adds the gridDim.x partials in block order, writes *dst and resets
+// the counter.  Deterministic: the order of the final sum does not depend on
+// which block finishes last.
+__device__ __forceinline__ void grid_sum_last(double s, double *part, unsigned *counter, double *dst) {
   __shared__ double sh[256];
+  __shared__ bool last;
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {
     if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = sh[0];
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) t += ((volatile double *)part)[i];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int k = 128; k > 0; k >>= 1) {
+    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { *dst = sh[0]; *counter = 0u; }
 }
 
 // y = A v - (beta/oldb) r1 (A v given in av), partial dots of v.y
 __global__ void k_y_upd1(const double *av, double *y, const double *r1, const double *v, long n,
-                         const double *st, double *part) {
+                         double *st, double *part, unsigned *counter) {
   if (st[S_ACTIVE] == 0.0) return;
   const double coef = st[S_BOVERO];
   double s = 0.0;
@@ -605,7 +684,7 @@ __global__ void k_y_upd1(const double *av, double *y, const double *r1, const do
     y[i] = yi;
     s += v[i] * yi;
   }
-  block_partial(s, part);
+  grid_sum_last(s, part, counter, st + S_ALFA);   // alfa = v . y
 }
 
 __global__ void k_y_upd2(double *y, const double *r2, long n, const double *st) {
@@ -615,31 +694,14 @@ __global__ void k_y_upd2(double *y, const double *r2, long n, const double *st) 
   y[i] -= (st[S_ALFA] * st[S_INVBETA]) * r2[i];
 }
 
-// y = M^{-1} r2 (given in mr) and partial dots of r2.y
-__global__ void k_dot_copy(const double *r2, const double *mr, double *y, long n, const double *st,
-                           double *part) {
+// beta2 = r2 . y with y = M^{-1} r2 already in place
+__global__ void k_dot_active(const double *r2, const double *y, long n, double *st, double *part,
+                             unsigned *counter) {
   if (st[S_ACTIVE] == 0.0) return;
   double s = 0.0;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-    const double yi = mr[i];
-    y[i] = yi;
-    s += r2[i] * yi;
-  }
-  block_partial(s, part);
-}
-
-__global__ void k_sum_active(const double *part, int nb, double *st, int slot) {
-  if (st[S_ACTIVE] == 0.0) return;
-  __shared__ double sh[1024];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) st[slot] = sh[0];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    s += r2[i] * y[i];
+  grid_sum_last(s, part, counter, st + S_BETA2);
 }
 
 __global__ void k_minres_scalars(double *st, double tol) {
@@ -679,14 +741,17 @@ __global__ void k_minres_scalars(double *st, double tol) {
   else if (rel <= tol && st[S_ITN] >= st[S_NEXTCHECK]) st[S_FLAG] = 1.0;
 }
 
-__global__ void k_w_upd(const double *v, const double *w1, const double *w2, double *wn, double *x,
-                        long n, const double *st) {
+// w = (v - oldeps w1 - delta w2) / gamma, x += phi w, and the next Lanczos
+// vector v = y_next / beta_next (S_INVBETA already holds 1 / beta_next)
+__global__ void k_w_upd(double *v, const double *w1, const double *w2, double *wn, double *x,
+                        const double *ynext, long n, const double *st) {
   if (st[S_ACTIVE] == 0.0) return;
   long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double w = (v[i] - st[S_OLDEPS] * w1[i] - st[S_DELTA] * w2[i]) * st[S_INVGAMMA];
   wn[i] = w;
   x[i] += st[S_PHI] * w;
+  v[i] = ynext[i] * st[S_INVBETA];
 }
 
 __global__ void k_sub(const double *a, const double *b, double *out, long n) {
@@ -724,8 +789,8 @@ static afi_status enqueue_iteration(afi_ctx *c, const MinresBufs &M, long t, cud
   double *st = c->small;
   double *r1 = M.B[t % 3], *r2 = M.B[(t + 1) % 3], *y = M.B[(t + 2) % 3];
   double *w1 = M.W[t % 2], *w2 = M.W[(t + 1) % 2];
+  unsigned *cnt = reinterpret_cast<unsigned *>(c->small + kCounters);
   launch(k_iter_begin, 1, 1, 0, s, st);
-  launch(k_v_from_y, nblk(nt), 256, 0, s, (const double *)y, M.v, nt, (const double *)st);
   // the heavy operator kernels skip their work in inactive iterations
   struct GateScope {
     afi_ctx *c;
@@ -734,17 +799,16 @@ static afi_status enqueue_iteration(afi_ctx *c, const MinresBufs &M, long t, cud
   } gate_scope(c, st + S_ACTIVE);
   AFI_TRY(op_saddle(c, M.v, M.tA, s));
   launch(k_y_upd1, kDotBlocks, 256, 0, s, (const double *)M.tA, y, (const double *)r1,
-         (const double *)M.v, nt, (const double *)st, c->small + kPart);
-  launch(k_sum_active, 1, 1024, 0, s, (const double *)(c->small + kPart), kDotBlocks, st, (int)S_ALFA);
+         (const double *)M.v, nt, st, c->small + kPart, cnt);
   launch(k_y_upd2, nblk(nt), 256, 0, s, y, (const double *)r2, nt, (const double *)st);
-  // roles now: r1' = r2, r2' = y, y' = r1
-  AFI_TRY(op_precond(c, y, M.tB, s));
-  launch(k_dot_copy, kDotBlocks, 256, 0, s, (const double *)y, (const double *)M.tB, r1, nt,
-         (const double *)st, c->small + kPart);
-  launch(k_sum_active, 1, 1024, 0, s, (const double *)(c->small + kPart), kDotBlocks, st, (int)S_BETA2);
+  // roles now: r1' = r2, r2' = y, y' = r1 (r1 is free: the preconditioner
+  // writes y' there directly)
+  AFI_TRY(op_precond(c, y, r1, s));
+  launch(k_dot_active, kDotBlocks, 256, 0, s, (const double *)y, (const double *)r1, nt, st,
+         c->small + kPart, cnt + 1);
   launch(k_minres_scalars, 1, 1, 0, s, st, c->opt.tol);
-  launch(k_w_upd, nblk(nt), 256, 0, s, (const double *)M.v, (const double *)w1, (const double *)w2,
-         w1, M.x, nt, (const double *)st);
+  launch(k_w_upd, nblk(nt), 256, 0, s, M.v, (const double *)w1, (const double *)w2, w1, M.x,
+         (const double *)r1, nt, (const double *)st);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -810,6 +874,7 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   AFI_TRY(dot(c, M.B[0], M.B[2], nt, st + S_BETA2, s));
   AFI_TRY(dot(c, M.b, M.b, nt, st + S_BNORM2, s));
   launch(k_minres_init, 1, 1, 0, s, st, (double)c->opt.maxit);
+  launch(k_v_from_y, nblk(nt), 256, 0, s, (const double *)M.B[2], M.v, nt, (const double *)st);
   AFI_LAUNCH_CHECK();
   const bool use_graph = c->opt.use_graph != 0;
   if (use_graph) {

@@ -460,7 +460,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     AFI_TRY(small_inverses(c, c->RtR_inv, nm, NP));
     afi_status st = AFI_OK;
     double *lscratch = nullptr;
-    AFI_CUDA(cudaMalloc(&lscratch, (size_t)c->ng * c->ng * sizeof(double)));
+    AFI_CUDA(cudaMalloc(&lscratch, ((size_t)c->ng * c->ng + c->ng) * sizeof(double)));
     if (c->n_c > 0) st = dense_spd_inverse(c, c->GtG, c->GtG_inv, c->ng, lscratch);
     cudaFree(lscratch);
     cudaFree(dptr); cudaFree(dkk); cudaFree(dent);
