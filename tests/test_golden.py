@@ -1,0 +1,62 @@
+"""The oracle against stored values the mathematics fixes (tests/golden/):
+closed-form Gauss-Legendre rules, and univariate B-spline matrices in exact
+rational arithmetic (written by tests/golden/make_univariate.py, which shares
+no code with the oracle)."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+
+from oracle import spline
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _gauss_cases():
+    cases, cur = {}, None
+    for ln in open(os.path.join(HERE, "gauss_legendre.txt")):
+        ln = ln.strip()
+        if not ln or ln.startswith("#"):
+            continue
+        if ln.startswith("n "):
+            cur = int(ln.split()[1])
+            cases[cur] = []
+            continue
+        x, w = ln.split()
+        env = {"sqrt": math.sqrt}
+        cases[cur].append((eval(x, env), eval(w, env)))
+    return cases
+
+
+def test_gauss_legendre_closed_forms():
+    for n, pw in _gauss_cases().items():
+        x, w = spline.gauss(n)                       # oracle rule on [0, 1]
+        ref_x = np.array([0.5 * (p + 1.0) for p, _ in pw])
+        ref_w = np.array([0.5 * q for _, q in pw])
+        o = np.argsort(x)
+        assert np.allclose(x[o], ref_x, rtol=0, atol=1e-15)
+        assert np.allclose(w[o], ref_w, rtol=0, atol=1e-15)
+
+
+def _univariate_cases():
+    lines = [ln.strip() for ln in open(os.path.join(HERE, "univariate_exact.txt"))
+             if ln.strip() and not ln.startswith("#")]
+    cases, i = [], 0
+    while i < len(lines):
+        _, p, nel = lines[i].split()
+        p, nel = int(p), int(nel)
+        n = nel + p
+        rows = [[float(Fraction(t)) for t in lines[i + 1 + r].split()] for r in range(2 * n)]
+        cases.append((p, nel, np.array(rows[:n]), np.array(rows[n:])))
+        i += 1 + 2 * n
+    return cases
+
+
+def test_univariate_matrices_exact():
+    cases = _univariate_cases()
+    assert [(p, nel) for p, nel, _, _ in cases] == [(2, 2), (2, 3), (3, 3), (4, 5)]
+    for p, nel, M, K in cases:
+        Ko, Mo = spline.univariate_matrices(nel, p)
+        assert np.allclose(Mo, M, rtol=0, atol=1e-14)
+        assert np.allclose(Ko, K, rtol=0, atol=1e-12)
