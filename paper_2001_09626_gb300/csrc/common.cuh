@@ -175,7 +175,11 @@ struct afi_ctx {
   int *bt_ent = nullptr;         // row*2 + (sign < 0)
   long n_shell = 0;
   int *prow_ptr = nullptr;       // per patch: rows touching the patch
-  int2 *prow_ent = nullptr;      // (row*2 + neg, dof)
+  int2 *prow_ent = nullptr;      // (row*2 + neg, dof); the dof becomes its component
+                                 // once rigid_tables has run
+  double2 *prow_coef = nullptr;  // rotation coefficients (v1, v2) of each entry
+  int2 *row_cp = nullptr;        // per row: (patch*4 + component) of copy A, of copy B or -1
+  double4_32a *row_cv = nullptr;     // per row: (v1, v2) of copy A, (v1, v2) of copy B
   int *pair_ptr = nullptr;       // G^T G off-diagonal pair blocks
   int2 *pair_kk = nullptr;       // (k, k')
   int4 *pair_ent = nullptr;      // (dofA, dofB, sign product, unused)
@@ -198,6 +202,8 @@ struct afi_ctx {
   // captured MINRES iterations (cudaGraphExec_t), rebuilt when prec changes
   void *graph_exec = nullptr;
   void *cap_stream = nullptr;        // private stream used only for capture
+  void *aux_stream = nullptr;        // second stream for independent operator branches
+  void *ev_fork = nullptr, *ev_join = nullptr;   // fork / join events of aux_stream
   const double *gate = nullptr;      // while enqueueing MINRES: device 'active' flag
   afi::TcSplit tcsplit[2][2];        // [interior][bf16]
   long long graph_nodes = 0;
@@ -231,6 +237,7 @@ afi_status op_Rt(afi_ctx *c, const double *x, double *g, cudaStream_t s);
 afi_status op_dense_inv(afi_ctx *c, const double *g, double *y, cudaStream_t s);
 afi_status op_G(afi_ctx *c, const double *y, double *out, bool subtract, cudaStream_t s);
 afi_status op_R_sub(afi_ctx *c, const double *y, double *v, cudaStream_t s);
+afi_status rigid_tables(afi_ctx *c);
 afi_status op_PS(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status op_precond(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status op_saddle(afi_ctx *c, const double *x, double *y, cudaStream_t s);

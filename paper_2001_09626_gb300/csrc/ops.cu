@@ -284,34 +284,33 @@ __device__ __forceinline__ bool last_block(unsigned *counter) {
 
 // Partial sums of (G^T x) over a strided part of the rows touching patch k:
 // part[(k * kGtBlocks + b) * NM + a].  Each entry touches its translation
-// and two rotations only (rigid_nz); the lists are sorted by dof, so a warp
-// mostly sees one component.
+// and two rotations only, with the rotation coefficients precomputed per
+// entry (ent[e] = (row*2 + neg, component), coef[e] = (v1, v2), see
+// rigid_nz); the lists are sorted by dof, so a warp mostly sees one
+// component.
 template <int NM>
-__global__ void __launch_bounds__(256) k_Gt_part(const DevPatch *P, const double *ctrl,
-                                                 const int *ptr, const int2 *ent, const double *x,
-                                                 double *part, int dim, unsigned *counter,
+__global__ void __launch_bounds__(256) k_Gt_part(const int *ptr, const int2 *ent, const double2 *coef,
+                                                 const double *x, double *part, unsigned *counter,
                                                  double *g, const double *gate) {
   if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   __shared__ double sh[8 * NM];
   const int k = blockIdx.y, b = blockIdx.x;
-  const DevPatch pt = P[k];
   double acc[NM];
 #pragma unroll
   for (int a = 0; a < NM; ++a) acc[a] = 0.0;
 #pragma unroll 4
   for (int e = ptr[k] + b * blockDim.x + threadIdx.x; e < ptr[k + 1]; e += gridDim.x * blockDim.x) {
-    int2 en = ent[e];
+    const int2 en = ent[e];
+    const double2 cf = coef[e];
     double xv = x[en.x >> 1];
     if (en.x & 1) xv = -xv;
-    int comp;
-    const double *X = dof_point(pt, ctrl, en.y, dim, comp);
     if (NM == 6) {
-      if (comp == 0) { acc[0] += xv; acc[4] += xv * X[2]; acc[5] += xv * X[1]; }
-      else if (comp == 1) { acc[1] += xv; acc[3] += xv * X[2]; acc[5] -= xv * X[0]; }
-      else { acc[2] += xv; acc[3] -= xv * X[1]; acc[4] -= xv * X[0]; }
+      if (en.y == 0) { acc[0] += xv; acc[4] += xv * cf.x; acc[5] += xv * cf.y; }
+      else if (en.y == 1) { acc[1] += xv; acc[3] += xv * cf.x; acc[5] += xv * cf.y; }
+      else { acc[2] += xv; acc[3] += xv * cf.x; acc[4] += xv * cf.y; }
     } else {
-      if (comp == 0) { acc[0] += xv; acc[2] += xv * X[1]; }
-      else { acc[1] += xv; acc[2] -= xv * X[0]; }
+      if (en.y == 0) { acc[0] += xv; acc[2] += xv * cf.x; }
+      else { acc[1] += xv; acc[2] += xv * cf.x; }
     }
   }
   block_sum_multi<256>(acc, NM, sh);
@@ -319,12 +318,12 @@ __global__ void __launch_bounds__(256) k_Gt_part(const DevPatch *P, const double
     for (int a = 0; a < NM; ++a) part[((long long)k * gridDim.x + b) * NM + a] = acc[a];
   // g[k][a] = sum over the blocks of patch k, in block order
   if (!last_block(counter)) return;
+  // (L2 loads: the partials were written by other blocks of this launch)
   const int npatch = gridDim.y;
-  const volatile double *vp = part;
   for (int e = threadIdx.x; e < npatch * NM; e += blockDim.x) {
     const int kk = e / NM, a = e - kk * NM;
     double sum = 0.0;
-    for (int bb = 0; bb < (int)gridDim.x; ++bb) sum += vp[((long long)kk * gridDim.x + bb) * NM + a];
+    for (int bb = 0; bb < (int)gridDim.x; ++bb) sum += __ldcg(part + ((long long)kk * gridDim.x + bb) * NM + a);
     g[e] = sum;
   }
 }
@@ -356,7 +355,6 @@ __global__ void __launch_bounds__(256) k_Rt_part(const DevPatch *P, const double
   // per patch: the modes' sums over components and chunks (fixed order),
   // then optionally Minv_k times them
   if (!last_block(counter)) return;
-  const volatile double *vp = part;
   const int nch = gridDim.x;
   for (int kk = threadIdx.x; kk < (int)gridDim.z; kk += blockDim.x) {
     double t[6] = {0, 0, 0, 0, 0, 0};
@@ -365,7 +363,7 @@ __global__ void __launch_bounds__(256) k_Rt_part(const DevPatch *P, const double
       const RigidNZ r = rigid_nz(cp, X0, dim);   // only the mode indices are used
       double q[3] = {0.0, 0.0, 0.0};
       for (int c2 = 0; c2 < nch; ++c2)
-        for (int a = 0; a < 3; ++a) q[a] += vp[(((long long)kk * dim + cp) * nch + c2) * 3 + a];
+        for (int a = 0; a < 3; ++a) q[a] += __ldcg(part + (((long long)kk * dim + cp) * nch + c2) * 3 + a);
       t[cp] += q[0];
       t[r.m1] += q[1];
       if (dim == 3) t[r.m2] += q[2];
@@ -417,43 +415,104 @@ __device__ __forceinline__ double rigid_apply(int comp, const double *X, const d
 }
 
 // out[r] (= or -=) sum over the row's copies of sign * (R_k y_k)(copy).
-__global__ void k_G(const DevPatch *P, const double *ctrl, const int2 *rc, const int2 *rk, long n_c,
-                    const double *y, double *out, int dim, int nm, int subtract, const double *src, const double *gate) {
+// out[r] (= or -=) sum over the row's copies of sign * (R_k y_k)(copy), with
+// the copies' (patch * 4 + component) in cp[r] and their rotation
+// coefficients (v1, v2 per copy) in cv[r].
+__global__ void k_G(const int2 *cp, const double4_32a *cv, long n_c, const double *y, double *out, int dim,
+                    int nm, int subtract, const double *src, const double *gate) {
   if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= n_c) return;
-  int2 e = rc[r], kk = rk[r];
-  double v;
-  {
-    const DevPatch pa = P[kk.x];
-    int comp;
-    const double *X = dof_point(pa, ctrl, e.x, dim, comp);
-    v = rigid_apply(comp, X, y + kk.x * nm, dim);
-  }
+  const int2 e = cp[r];
+  const double4_32a v4 = cv[r];
+  const double X0[3] = {0.0, 0.0, 0.0};
+  const double *ya = y + (e.x >> 2) * nm;
+  RigidNZ ra = rigid_nz(e.x & 3, X0, dim);   // mode indices only
+  double v = ya[e.x & 3] + v4.x * ya[ra.m1] + v4.y * ya[ra.m2];
   if (e.y >= 0) {
-    const DevPatch pb = P[kk.y];
-    int comp;
-    const double *X = dof_point(pb, ctrl, e.y, dim, comp);
-    v -= rigid_apply(comp, X, y + kk.y * nm, dim);
+    const double *yb = y + (e.y >> 2) * nm;
+    RigidNZ rb = rigid_nz(e.y & 3, X0, dim);
+    v -= yb[e.y & 3] + v4.z * yb[rb.m1] + v4.w * yb[rb.m2];
   }
   out[r] = subtract ? src[r] - v : v;
+}
+
+// Rotation coefficients of G = B R, once at setup: per constraint row the
+// (patch * 4 + component) and (v1, v2) of both copies, and per entry of the
+// per-patch row lists the component and (v1, v2) of its dof.
+__global__ void k_rigid_tables(const DevPatch *P, const double *ctrl, const int2 *rc, const int2 *rk,
+                               long n_c, int2 *cp, double4_32a *cv, const int *pptr, int2 *pent,
+                               double2 *pcoef, int npatch, int dim) {
+  const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (t < n_c) {
+    const int2 e = rc[t], kk = rk[t];
+    int ca, cb;
+    const double *Xa = dof_point(P[kk.x], ctrl, e.x, dim, ca);
+    const RigidNZ a = rigid_nz(ca, Xa, dim);
+    double4_32a v = make_double4_32a(a.v1, dim == 3 ? a.v2 : 0.0, 0.0, 0.0);
+    int2 c2 = make_int2(kk.x * 4 + ca, -1);
+    if (e.y >= 0) {
+      const double *Xb = dof_point(P[kk.y], ctrl, e.y, dim, cb);
+      const RigidNZ b = rigid_nz(cb, Xb, dim);
+      v.z = b.v1;
+      v.w = dim == 3 ? b.v2 : 0.0;
+      c2.y = kk.y * 4 + cb;
+    }
+    cp[t] = c2;
+    cv[t] = v;
+  }
+  // entries of the per-patch lists: patch k owns [pptr[k], pptr[k+1])
+  const long ne = pptr[npatch];
+  for (long e = t; e < ne; e += (long)gridDim.x * blockDim.x) {
+    int lo = 0, hi = npatch;   // the patch of entry e
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (pptr[mid] <= e) lo = mid; else hi = mid;
+    }
+    int comp;
+    const double *X = dof_point(P[lo], ctrl, pent[e].y, dim, comp);
+    const RigidNZ r = rigid_nz(comp, X, dim);
+    pcoef[e] = make_double2(r.v1, dim == 3 ? r.v2 : 0.0);
+    pent[e].y = comp;
+  }
+}
+
+afi_status rigid_tables(afi_ctx *c) {
+  if (c->n_c == 0) return AFI_OK;
+  AFI_TRY(dalloc(c, (void **)&c->row_cp, (size_t)c->n_c * sizeof(int2)));
+  AFI_TRY(dalloc(c, (void **)&c->row_cv, (size_t)c->n_c * sizeof(double4_32a)));
+  int ne = 0;
+  AFI_CUDA(cudaMemcpy(&ne, c->prow_ptr + c->npatch, sizeof(int), cudaMemcpyDeviceToHost));
+  AFI_TRY(dalloc(c, (void **)&c->prow_coef, (size_t)std::max(ne, 1) * sizeof(double2)));
+  const long nt = std::max((long)ne, c->n_c);
+  launch(k_rigid_tables, (unsigned)((nt + 255) / 256), 256, 0, 0, (const DevPatch *)c->patches,
+         (const double *)c->ctrl, (const int2 *)c->row_copy, (const int2 *)c->row_patch, c->n_c,
+         c->row_cp, c->row_cv, (const int *)c->prow_ptr, c->prow_ent, c->prow_coef, c->npatch, c->dim);
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
 }
 
 afi_status op_Gt_rows(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
   dim3 gr(kGtBlocks, c->npatch);
   unsigned *cnt = reinterpret_cast<unsigned *>(c->small + kCounters) + 2;
   if (c->nm == 6)
-    launch(k_Gt_part<6>, gr, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, c->part, c->dim, cnt, g, (const double *)c->gate);
+    launch(k_Gt_part<6>, gr, 256, 0, s, (const int *)c->prow_ptr, (const int2 *)c->prow_ent,
+           (const double2 *)c->prow_coef, x, c->part, cnt, g, (const double *)c->gate);
   else
-    launch(k_Gt_part<3>, gr, 256, 0, s, c->patches, c->ctrl, c->prow_ptr, c->prow_ent, x, c->part, c->dim, cnt, g, (const double *)c->gate);
+    launch(k_Gt_part<3>, gr, 256, 0, s, (const int *)c->prow_ptr, (const int2 *)c->prow_ent,
+           (const double2 *)c->prow_coef, x, c->part, cnt, g, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 // g = R^T v per patch; with Minv, g = Minv_k (R_k^T v) instead.
+// The P_u reductions use their own slice of c->part, ticket and g buffer, so
+// that they can run concurrently with the P_chi reductions (op_precond).
+static double *pu_part(afi_ctx *c) { return c->part + 64LL * c->npatch; }
+
 static afi_status Rt_apply(afi_ctx *c, const double *x, double *g, const double *Minv, cudaStream_t s) {
   unsigned *cnt = reinterpret_cast<unsigned *>(c->small + kCounters) + 3;
-  launch(k_Rt_part, dim3(kRtChunks, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x, c->part,
+  launch(k_Rt_part, dim3(kRtChunks, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x, pu_part(c),
          c->dim, cnt, c->nm, g, Minv, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
@@ -483,9 +542,9 @@ afi_status op_Pchi(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
 }
 
 static afi_status G_apply(afi_ctx *c, const double *y, double *out, const double *src, cudaStream_t s) {
-  launch(k_G, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->patches, c->ctrl, c->row_copy,
-                                                       c->row_patch, c->n_c, y, out, c->dim,
-                                                       c->nm, src ? 1 : 0, src, (const double *)c->gate);
+  launch(k_G, (unsigned)((c->n_c + 255) / 256), 256, 0, s, (const int2 *)c->row_cp,
+         (const double4_32a *)c->row_cv, c->n_c, y, out, c->dim, c->nm, src ? 1 : 0, src,
+         (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -496,7 +555,7 @@ afi_status op_G(afi_ctx *c, const double *y, double *out, bool subtract, cudaStr
 
 afi_status op_Pu(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   // P_u x = x - R (R^T R)^{-1} R^T x, patch by patch
-  double *g = gbuf(c, 0);
+  double *g = gbuf(c, 2);
   AFI_TRY(Rt_apply(c, x, g, c->RtR_inv, s));
   launch(k_Rsub, dim3((c->max_N + 255) / 256, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x,
          y, (const double *)g, c->dim, c->nm, (const double *)c->gate);
@@ -564,31 +623,67 @@ afi_status op_PS(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   return AFI_OK;
 }
 
+// Independent branches of an operator run on the context's second stream:
+// fork() makes it wait for everything enqueued on s so far, join() makes s
+// wait for the branch.  Under stream capture this records a fork and a join
+// in the graph.
+static afi_status fork_aux(afi_ctx *c, cudaStream_t s, cudaStream_t *aux) {
+  *aux = (cudaStream_t)c->aux_stream;
+  AFI_CUDA(cudaEventRecord((cudaEvent_t)c->ev_fork, s));
+  AFI_CUDA(cudaStreamWaitEvent(*aux, (cudaEvent_t)c->ev_fork, 0));
+  return AFI_OK;
+}
+
+static afi_status join_aux(afi_ctx *c, cudaStream_t s, cudaStream_t aux) {
+  AFI_CUDA(cudaEventRecord((cudaEvent_t)c->ev_join, aux));
+  AFI_CUDA(cudaStreamWaitEvent(s, (cudaEvent_t)c->ev_join, 0));
+  return AFI_OK;
+}
+
+// The multiplier branch of the preconditioner may run beside the primal one
+// unless both would use the local-solver scratch slab (Schur block tensors
+// too large for shared memory).
+static bool precond_branches_independent(const afi_ctx *c) {
+  const size_t esz = (c->opt.prec == AFI_FD_FP64) ? sizeof(double) : sizeof(float);
+  return 4ull * c->max_N * esz <= (size_t)c->smem_optin;
+}
+
 afi_status op_precond(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
-  // calB^{-1} = blkdiag(P_u P_A^{-1} P_u^T, P_chi P_S P_chi^T), eq. (4.9)
+  // calB^{-1} = blkdiag(P_u P_A^{-1} P_u^T, P_chi P_S P_chi^T), eq. (4.9); the
+  // two diagonal blocks are independent
   const long n = c->n_dof;
   double *t1 = c->ws + 3 * n + c->n_c, *m2 = c->ws + 4 * n + c->n_c;
+  cudaStream_t a = s;
+  const bool two = c->n_c > 0 && precond_branches_independent(c);
+  if (two) AFI_TRY(fork_aux(c, s, &a));
+  if (c->n_c > 0) {
+    AFI_TRY(op_Pchi(c, x + n, m2, a));
+    AFI_TRY(op_PS(c, m2, y + n, a));
+    AFI_TRY(op_Pchi(c, y + n, y + n, a));
+  }
   AFI_TRY(op_Pu(c, x, t1, s));
   AFI_TRY(fd_run(c, 0, t1, y, s));
   AFI_TRY(op_Pu(c, y, y, s));
-  if (c->n_c > 0) {
-    AFI_TRY(op_Pchi(c, x + n, m2, s));
-    AFI_TRY(op_PS(c, m2, y + n, s));
-    AFI_TRY(op_Pchi(c, y + n, y + n, s));
-  }
+  if (two) AFI_TRY(join_aux(c, s, a));
   return AFI_OK;
 }
 
 afi_status op_saddle(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
-  // [A w + B^T P_chi chi ; P_chi B w], eq. (4.7)
+  // [A w + B^T P_chi chi ; P_chi B w], eq. (4.7); the multiplier products
+  // run beside the stiffness matvec
   const long n = c->n_dof;
   double *m2 = c->ws + 4 * n + 2 * c->n_c, *m3 = m2 + c->n_c;
+  cudaStream_t a = s;
+  if (c->n_c > 0) {
+    AFI_TRY(fork_aux(c, s, &a));
+    AFI_TRY(op_Pchi(c, x + n, m2, a));
+    AFI_TRY(op_B(c, x, m3, a));
+    AFI_TRY(op_Pchi(c, m3, y + n, a));
+  }
   AFI_TRY(op_stiffness(c, x, y, s));
   if (c->n_c > 0) {
-    AFI_TRY(op_Pchi(c, x + n, m2, s));
+    AFI_TRY(join_aux(c, s, a));
     AFI_TRY(op_Bt(c, m2, y, true, false, s));
-    AFI_TRY(op_B(c, x, m3, s));
-    AFI_TRY(op_Pchi(c, m3, y + n, s));
   }
   return AFI_OK;
 }
@@ -663,7 +758,7 @@ __device__ __forceinline__ void grid_sum_last(double s, double *part, unsigned *
   if (!last) return;
   __threadfence();
   double t = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) t += ((volatile double *)part)[i];
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) t += __ldcg(part + i);
   sh[threadIdx.x] = t;
   __syncthreads();
   for (int k = 128; k > 0; k >>= 1) {

@@ -418,6 +418,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   AFI_TRY(upload(c, &c->bt_ent, bte));
   AFI_TRY(upload(c, &c->prow_ptr, pptr));
   AFI_TRY(upload(c, &c->prow_ent, pent));
+  AFI_TRY(rigid_tables(c));
 
   // ---- G^T G (diagonal blocks from the per-patch lists, off-diagonal from
   //      the patch pairs) and its inverse; R^T R per patch and its inverse
@@ -480,9 +481,16 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   AFI_CUDA(cudaMemset(c->small, 0, kSmallDoubles * sizeof(double)));
   AFI_CUDA(cudaMallocHost((void **)&c->host_small, 128 * sizeof(double)));
   {
-    cudaStream_t cs = nullptr;
+    cudaStream_t cs = nullptr, as = nullptr;
     AFI_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     c->cap_stream = cs;
+    AFI_CUDA(cudaStreamCreateWithFlags(&as, cudaStreamNonBlocking));
+    c->aux_stream = as;
+    cudaEvent_t ef = nullptr, ej = nullptr;
+    AFI_CUDA(cudaEventCreateWithFlags(&ef, cudaEventDisableTiming));
+    AFI_CUDA(cudaEventCreateWithFlags(&ej, cudaEventDisableTiming));
+    c->ev_fork = ef;
+    c->ev_join = ej;
   }
   AFI_CUDA(cudaDeviceSynchronize());
   auto t1 = std::chrono::steady_clock::now();
@@ -493,6 +501,9 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
 void free_context(afi_ctx *c) {
   if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
   if (c->cap_stream) cudaStreamDestroy((cudaStream_t)c->cap_stream);
+  if (c->aux_stream) cudaStreamDestroy((cudaStream_t)c->aux_stream);
+  if (c->ev_fork) cudaEventDestroy((cudaEvent_t)c->ev_fork);
+  if (c->ev_join) cudaEventDestroy((cudaEvent_t)c->ev_join);
   void *ptrs[] = {c->patches, c->tabs, c->dpool, c->fpool, c->bpool, c->tcpool, c->ctrl, c->stencil,
                   c->qgeo, c->row_copy, c->row_grp, c->row_patch, c->shell_dof, c->bt_ptr,
                   c->bt_ent, c->prow_ptr, c->prow_ent, c->pair_ptr, c->pair_kk, c->pair_ent,
@@ -502,7 +513,7 @@ void free_context(afi_ctx *c) {
                   c->tcsplit[1][1].d_tc, c->tcsplit[1][1].d_simt, c->tcsplit[0][0].d_plane,
                   c->tcsplit[0][0].d_line, c->tcsplit[0][1].d_plane, c->tcsplit[0][1].d_line,
                   c->tcsplit[1][0].d_plane, c->tcsplit[1][0].d_line, c->tcsplit[1][1].d_plane,
-                  c->tcsplit[1][1].d_line};
+                  c->tcsplit[1][1].d_line, c->prow_coef, c->row_cp, c->row_cv};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);
