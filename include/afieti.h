@@ -238,6 +238,20 @@ const char *afi_last_error(void);
  * launches in between. */
 long long afi_kernel_launches(void);
 
+/* Self-test of the library's failure path for tensor-core waits (no
+ * counterpart in the paper).  Every tcgen05 kernel waits on mbarriers (TMA
+ * and MMA completion) with a bounded number of polls; when a wait runs out
+ * the kernel frees its tensor memory, returns, and the operation reports
+ * AFI_ETIMEOUT instead of hanging the GPU.  This entry point runs that path
+ * on purpose: one CTA allocates tensor memory, waits at most `polls` polls
+ * (1 <= polls <= 2^22) on an mbarrier that nothing ever arrives on, frees
+ * the tensor memory and returns.  Returns AFI_ETIMEOUT when the wait ran out
+ * (the expected outcome), AFI_OK if it completed, AFI_EINVAL for polls out
+ * of range, AFI_ECUDA on a CUDA error.  *polls_used (may be NULL) receives
+ * the number of polls made.  Synchronous on the legacy default stream;
+ * allocates and frees 16 bytes of device memory. */
+afi_status afi_selftest_bounded_wait(long long polls, long long *polls_used);
+
 #ifdef __cplusplus
 }
 #endif

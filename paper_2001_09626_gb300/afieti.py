@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": AFI_FD_FP64, "fp32": AFI_FD_FP32, "tf32": AFI_FD_TF32, "bf
 EXPORTED = ["af_ieti_setup", "fd_apply", "ieti_solve", "ieti_solve_adjoint", "afi_lame_grad",
             "afi_load_vector", "afi_apply", "afi_set_precision", "afi_sizes", "afi_memory",
             "af_ieti_destroy", "afi_status_string", "afi_last_error", "afi_kernel_launches",
-            "afi_fd_apply_static"]
+            "afi_fd_apply_static", "afi_selftest_bounded_wait"]
 
 
 class afi_problem(C.Structure):
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.afi_fd_apply_static.argtypes = [ip, ip, ip, dp, dp, dp, dp, dp, dp,
                                          C.POINTER(C.c_double), C.c_double, C.c_double, dp, dp,
                                          ip, vp]
+    lib.afi_selftest_bounded_wait.argtypes = [C.c_longlong, C.POINTER(C.c_longlong)]
     lib.afi_kernel_launches.argtypes = []
     lib.afi_kernel_launches.restype = C.c_longlong
     for name in EXPORTED:
@@ -109,6 +110,13 @@ def afi_last_error() -> str:
 
 def afi_kernel_launches() -> int:
     return int(load().afi_kernel_launches())
+
+
+def afi_selftest_bounded_wait(polls: int):
+    """Run the bounded-wait failure path once; returns (status, polls used)."""
+    used = C.c_longlong(0)
+    status = load().afi_selftest_bounded_wait(int(polls), C.byref(used))
+    return int(status), int(used.value)
 
 
 def _check(status, where, allow=()):

@@ -44,15 +44,26 @@ __device__ __forceinline__ void commit(uint64_t *mbar) {
       smem_u32(mbar)));
 }
 
-// bounded wait for the given phase of an mbarrier; false on timeout
-__device__ __forceinline__ bool wait_phase(uint64_t *mbar, uint32_t phase) {
+// bounded wait for the given phase of an mbarrier: at most `limit` polls
+// (each try_wait may suspend the thread for a short hardware-defined time);
+// false on timeout, *used = polls made
+__device__ __forceinline__ bool wait_phase_n(uint64_t *mbar, uint32_t phase, long long limit,
+                                             long long *used) {
   uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it)
+  long long it = 0;
+  for (; it < limit && !done; ++it)
     asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  "selp.u32 %0, 1, 0, p;\n}"
                  : "=r"(done)
                  : "r"(smem_u32(mbar)), "r"(phase));
+  *used = it;
   return done != 0;
+}
+
+// the waits of the tensor-core kernels: at most 2^22 polls
+__device__ __forceinline__ bool wait_phase(uint64_t *mbar, uint32_t phase) {
+  long long used;
+  return wait_phase_n(mbar, phase, 1LL << 22, &used);
 }
 
 // 32 lanes x 8 columns of 32 bits from tensor memory; completes at ld_wait()

@@ -53,6 +53,14 @@ def test_setup_rejects_invalid_problem_without_touching_the_device(lib):
     assert "invalid" in afieti.afi_last_error()
 
 
+def test_selftest_rejects_out_of_range_polls_without_touching_the_device(lib):
+    from paper_2001_09626_gb300 import afieti
+    for polls in (0, -5, (1 << 22) + 1):
+        status, used = afieti.afi_selftest_bounded_wait(polls)
+        assert status == afieti.AFI_EINVAL and used == 0
+    assert "polls" in afieti.afi_last_error()
+
+
 def test_no_oracle_on_product_path():
     """The package never imports the oracle."""
     pkg = os.path.join(ROOT, "paper_2001_09626_gb300")
