@@ -192,6 +192,8 @@ struct afi_ctx {
   // workspaces
   double *ws = nullptr; long long ws_n = 0;     // general FP64 workspace
   double *fdscratch = nullptr; long long fdscratch_n = 0;
+  double *ps_buf = nullptr;                     // Schur block: 4 n_dof doubles (v, o, t1, t2)
+  double *ps_rint = nullptr, *ps_vint = nullptr;   // Schur block: interior right side, solution
   double *small = nullptr;                      // reduction / scalar area
   double *part = nullptr;                       // per-patch partial sums
   double *host_small = nullptr;                 // pinned host mirror
@@ -260,6 +262,9 @@ afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaS
 afi_status fd_simt_list(afi_ctx *c, int interior, const int *list, int count, int maxN,
                         const double *r, double *s, cudaStream_t st, int nrhs);
 afi_status fd_tc_ready(afi_ctx *c);
+// true when the local-solver FD (full or interior tensors) at the context's
+// precision uses the shared local-solver scratch slab
+bool fd_uses_scratch(afi_ctx *c, int interior);
 afi_status fd_tc_tables(afi_ctx *c);
 // fd_slab.cu (three-pass tensor-core FD for tensors larger than one CTA)
 afi_status slab_prepare(afi_ctx *c, int *dyn_max);

@@ -418,6 +418,21 @@ afi_status fd_tc_tables(afi_ctx *c) {
   return AFI_OK;
 }
 
+bool fd_uses_scratch(afi_ctx *c, int interior) {
+  int maxN = 1;
+  for (auto &p : c->hp) maxN = std::max(maxN, interior ? p.Ni : p.N);
+  switch (c->opt.prec) {
+    case AFI_FD_FP64: return 2ull * maxN * sizeof(double) > (size_t)c->smem_optin;
+    case AFI_FD_FP32: return 2ull * maxN * sizeof(float) > (size_t)c->smem_optin;
+    default: {
+      const TcSplit &sp = c->tcsplit[interior][c->opt.prec == AFI_FD_BF16];
+      if (!sp.ready) return true;   // not known yet: assume it does
+      return sp.nplane > 0 ||
+             (sp.nsimt > 0 && 2ull * sp.simt_maxN * sizeof(float) > (size_t)c->smem_optin);
+    }
+  }
+}
+
 // Build every split up front (called before a CUDA graph is captured).
 afi_status fd_tc_ready(afi_ctx *c) {
   for (int in = 0; in < 2; ++in)

@@ -640,12 +640,11 @@ static afi_status join_aux(afi_ctx *c, cudaStream_t s, cudaStream_t aux) {
   return AFI_OK;
 }
 
-// The multiplier branch of the preconditioner may run beside the primal one
-// unless both would use the local-solver scratch slab (Schur block tensors
-// too large for shared memory).
-static bool precond_branches_independent(const afi_ctx *c) {
-  const size_t esz = (c->opt.prec == AFI_FD_FP64) ? sizeof(double) : sizeof(float);
-  return 4ull * c->max_N * esz <= (size_t)c->smem_optin;
+// The multiplier branch of the preconditioner (whose Schur block solves on
+// the interior tensors) may run beside the primal one (FD on the full
+// tensors) unless both local solves would use the local-solver scratch slab.
+static bool precond_branches_independent(afi_ctx *c) {
+  return !(fd_uses_scratch(c, 0) && fd_uses_scratch(c, 1));
 }
 
 afi_status op_precond(afi_ctx *c, const double *x, double *y, cudaStream_t s) {

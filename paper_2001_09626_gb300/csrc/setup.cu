@@ -476,6 +476,9 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   // 4 slabs per (patch, component) block in the widest precision
   c->fdscratch_n = 4LL * c->n_dof + 16;
   AFI_TRY(dalloc(c, (void **)&c->fdscratch, c->fdscratch_n * sizeof(double)));
+  AFI_TRY(dalloc(c, (void **)&c->ps_buf, (size_t)4 * c->n_dof * sizeof(double)));
+  AFI_TRY(dalloc(c, (void **)&c->ps_rint, (size_t)std::max(1L, c->n_int) * sizeof(double)));
+  AFI_TRY(dalloc(c, (void **)&c->ps_vint, (size_t)std::max(1L, c->n_int) * sizeof(double)));
   AFI_TRY(dalloc(c, (void **)&c->small, kSmallDoubles * sizeof(double)));
   AFI_TRY(dalloc(c, (void **)&c->part, (size_t)NP * 64 * 6 * sizeof(double)));
   AFI_CUDA(cudaMemset(c->small, 0, kSmallDoubles * sizeof(double)));
@@ -513,7 +516,8 @@ void free_context(afi_ctx *c) {
                   c->tcsplit[1][1].d_tc, c->tcsplit[1][1].d_simt, c->tcsplit[0][0].d_plane,
                   c->tcsplit[0][0].d_line, c->tcsplit[0][1].d_plane, c->tcsplit[0][1].d_line,
                   c->tcsplit[1][0].d_plane, c->tcsplit[1][0].d_line, c->tcsplit[1][1].d_plane,
-                  c->tcsplit[1][1].d_line, c->prow_coef, c->row_cp, c->row_cv};
+                  c->tcsplit[1][1].d_line, c->prow_coef, c->row_cp, c->row_cv, c->ps_buf,
+                  c->ps_rint, c->ps_vint};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);
