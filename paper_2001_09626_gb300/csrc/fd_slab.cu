@@ -77,6 +77,24 @@ template <> __device__ __forceinline__ void st4<1>(__nv_bfloat16 *p, const float
   *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(h);
 }
 
+// two consecutive inputs (aligned to their pair size) as FP32
+__device__ __forceinline__ void ld2(const double *p, float *v) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  v[0] = f64_to_f32(a.x); v[1] = f64_to_f32(a.y);
+}
+__device__ __forceinline__ void ld2(const float *p, float *v) {
+  const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+  v[0] = a.x; v[1] = a.y;
+}
+// two consecutive K entries of one operand row (8-byte / 4-byte aligned)
+template <int FMT> __device__ __forceinline__ void st2(typename Op<FMT>::T *p, const float *v);
+template <> __device__ __forceinline__ void st2<2>(float *p, const float *v) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+template <> __device__ __forceinline__ void st2<1>(__nv_bfloat16 *p, const float *v) {
+  *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v[0], v[1]);
+}
+
 __device__ __forceinline__ float ld_in(const double *p) { return f64_to_f32(__ldg(p)); }
 __device__ __forceinline__ float ld_in(const float *p) { return __ldg(p); }
 __device__ __forceinline__ void st_out(double *p, float v) { *p = f32_to_f64(v); }
@@ -162,6 +180,28 @@ __global__ void __launch_bounds__(256, 4) k_fd_plane(const DevPatch *P, const Ta
           const int idx = 4 * g;
           const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
           st4<FMT>(&A[cmp<FMT>(row, idx - row * n1, kch0)], v[u]);
+        }
+      }
+    }
+  } else if ((n1 & 1) == 0 && ((uintptr_t)in & (2 * sizeof(TIn) - 1)) == 0) {
+    // two consecutive i1 of one row per thread (even rows): 2-element
+    // global loads and one 8-byte (TF32) or 4-byte (BF16) shared store
+    constexpr int LB = 8;
+    const int N2 = N >> 1;
+    for (int g0 = tid; g0 < N2; g0 += LB * 256) {
+      float v[LB][2];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int g = g0 + u * 256;
+        if (g < N2) ld2(in + 2 * g, v[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int g = g0 + u * 256;
+        if (g < N2) {
+          const int idx = 2 * g;
+          const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
+          st2<FMT>(&A[cmp<FMT>(row, idx - row * n1, kch0)], v[u]);
         }
       }
     }
@@ -320,7 +360,40 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
   // operand: row = line (128), k = i3.  A warp moves 8 lines x 4 planes per
   // instruction: 32-byte runs in global memory, one 16-byte unit per row in
   // shared memory.
-  {
+  if ((LN & 3) == 0 && ((uintptr_t)X & 15) == 0) {
+    // aligned planes: a lane moves 4 consecutive lines of one plane with a
+    // 16-byte load (a warp: 16 lines x 8 planes per instruction)
+    const int l4 = lane & 3, k8 = lane >> 2;
+    const int nk8 = (n3 + 7) / 8, nitem = 8 * nk8;
+    constexpr int LB = 4;
+    for (int i0 = warp; i0 < nitem; i0 += 8 * LB) {
+      float v[LB][4];
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int it = i0 + u * 8;
+        const int rg = it % 8, kg = it / 8;
+        const int row = rg * 16 + l4 * 4, k = kg * 8 + k8;
+        const bool in = it < nitem && k < n3;
+        if (in && row + 3 < nl) {
+          ld4(X + (long long)k * LN + row, v[u]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            v[u][e] = (in && row + e < nl) ? __ldg(X + (long long)k * LN + row + e) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < LB; ++u) {
+        const int it = i0 + u * 8;
+        const int rg = it % 8, kg = it / 8;
+        const int row = rg * 16 + l4 * 4, k = kg * 8 + k8;
+        if (it < nitem && k < n3)
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (row + e < nl) A[cmp<FMT>(row + e, k, kch)] = Op<FMT>::cvt(v[u][e]);
+      }
+    }
+  } else {
     const int r8 = lane & 7, k4 = lane >> 3;
     const int nk4 = (n3 + 3) / 4, nitem = 16 * nk4;
     constexpr int LB = 8;

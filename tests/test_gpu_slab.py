@@ -2,10 +2,11 @@
 than one CTA) against the CPU oracle, through the C ABI.
 
 The context option AFI_VARIANT_FD_SLAB sends every 3D tensor through that
-path, so it is checked here on patches the oracle solves quickly: uneven
-sizes per direction (14 x 13 x 16 and 11 x 13 x 16 basis functions), so that
-the plane groups (128 // 14 = 9 planes: 9 + 7) and the 128-line tiles of the
-third-direction pass (182 lines: 128 + 54) both end in a ragged tail.
+path, so it is checked here on patches the oracle solves quickly.  The
+"uneven" shapes (14 x 13 x 16 and 11 x 13 x 16 basis functions) make the
+plane groups (128 // 14 = 9 planes: 9 + 7) and the 128-line tiles of the
+third-direction pass (182 lines: 128 + 54) end in a ragged tail; the
+"aligned" shapes (12 x 12 x 14 and 16 x 12 x 14) take the vectorized loads.
 Tolerances as in test_gpu_parity: TF32 1e-2, BF16 3e-2 per application."""
 import numpy as np
 import pytest
@@ -25,12 +26,18 @@ def T(x):
     return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
 
 
-@pytest.fixture(scope="module")
-def slab():
+# (a) odd and even row lengths, plane sizes not multiples of 4: scalar and
+#     two-wide loads; (b) rows and planes multiples of 4 (12x12x14, 16x12x14):
+#     four-wide plane loads and 16-byte line loads
+SHAPES = {"uneven": [[12, 9], [11], [14]], "aligned": [[10, 14], [10], [12]]}
+
+
+@pytest.fixture(scope="module", params=sorted(SHAPES))
+def slab(request):
     import __graft_entry__ as g
     g.build()
     from paper_2001_09626_gb300.solver import Solver
-    prob = W.quarter_annulus((2, 1, 1), 2, nel_cols=[[12, 9], [11], [14]], name="annulus-slab")
+    prob = W.quarter_annulus((2, 1, 1), 2, nel_cols=SHAPES[request.param], name="annulus-slab")
     orc = AFIETI(prob)
     s = Solver(prob, prec="tf32", tol=1e-8, local_only=True, fd_slab=True)
     ref = Solver(prob, prec="tf32", tol=1e-8, local_only=True)
