@@ -10,7 +10,10 @@ to 1e-8 relative residual (estimate and true FP64 residual).
 
 One step = one complete AF-IETI solve (lambda_0, MINRES, recovery) with the
 load vector resident in HBM.  The per-step inputs are larger than L2: every
-iteration streams the 10.8 GB FP64 stiffness stencil.
+iteration streams the 10.8 GB FP64 stiffness stencil.  As in the paper's
+INEXACT timings, the reported solve time includes the local-solver setup
+(Algorithm 1 step 1, timed once by the library and added to the measured
+solve); the stiffness assembly and constraint setup are reported as setup_s.
 
   python bench.py [--gpus N --steps K --warmup W --prec fp32|fp64|tf32|bf16]
   python bench.py --impl reference ...   (the CPU oracle as the reference arm)
@@ -279,8 +282,12 @@ def run_ours(args):
     barrier()
     launches = (A.afi_kernel_launches() - L0) // args.steps
     clocks = sampler.stop()
-    ms = reduce_max(e0.elapsed_time(e1) / args.steps, world)
+    ms_solve = reduce_max(e0.elapsed_time(e1) / args.steps, world)
     info = dict(s.last_info)
+    # one solve as the paper times INEXACT: MINRES plus the local-solver setup
+    # (Algorithm 1 step 1: univariate matrices, eigensolves, operand tables)
+    fd_setup_ms = reduce_max(float(info["t_fd_setup_ms"]), world)
+    ms = ms_solve + fd_setup_ms
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     f_h = f.cpu().pin_memory()
@@ -361,12 +368,15 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (10.8 GB stencil streamed each iteration)"},
             "iterations": info["iters"], "relres_true": info["relres_true"],
             "setup_s": round(setup_s, 3),
-            "plain_fp64": {"solve_s": round(ms_plain / 1e3, 4), "iterations": info_plain["iters"],
+            "solve_s_without_fd_setup": round(ms_solve / 1e3, 4),
+            "fd_setup_s": round(fd_setup_ms / 1e3, 4),
+            "plain_fp64": {"solve_s": round((ms_plain + fd_setup_ms) / 1e3, 4),
+                           "iterations": info_plain["iters"],
                            "relres_true": info_plain["relres_true"]},
             "fd_apply_dofs_per_s": {k: round(s.n_dof / (v * 1e-3), 1) for k, v in fd_ms.items()},
             "fd_apply_dofs_per_s_nrhs8": {k: round(8 * s.n_dof / (v * 1e-3), 1)
                                           for k, v in fd8_ms.items()},
-            "e2e": {"value": round(ms_e2e / 1e3, 4), "unit": "s",
+            "e2e": {"value": round((ms_e2e + fd_setup_ms) / 1e3, 4), "unit": "s",
                     "h2d_bytes_per_step": 8 * s.n_dof, "d2h_bytes_per_step": 8 * s.n_dof},
             "gpu_launches": int(launches), "roofline": roofline, "roofline_fd": roofline_fd,
             "clocks": clocks}

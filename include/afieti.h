@@ -111,11 +111,15 @@ typedef struct {
 
 /* Filled by ieti_solve / ieti_solve_adjoint (for the last right-hand side):
  * iterations, the MINRES estimate, the true relative residual, the setup
- * time of the context and the wall time of this solve (device events). */
+ * time of the context, the wall time of this solve (device events) and the
+ * part of the setup that builds the local solvers of Algorithm 1 (univariate
+ * matrices, generalised eigensolves of eq. 5.8, tensor-core operand tables,
+ * FD work splits; the paper counts this part in its solve times). */
 typedef struct {
   int iters;
   double relres_est, relres_true;
   double t_setup_ms, t_solve_ms;
+  double t_fd_setup_ms;
 } afi_info;
 
 /* Operators of the hot path, for afi_apply (each is one row of the solve):

@@ -39,7 +39,8 @@ class afi_options(C.Structure):
 
 class afi_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("relres_est", C.c_double), ("relres_true", C.c_double),
-                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("t_fd_setup_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -147,6 +147,7 @@ struct afi_ctx {
   long n_dof = 0, n_c = 0, n_int = 0;
   afi_options opt{};
   double t_setup_ms = 0.0;
+  double t_fd_setup_ms = 0.0;        // local-solver part of the setup (Algorithm 1 step 1)
 
   // host copies
   std::vector<afi::DevPatch> hp;

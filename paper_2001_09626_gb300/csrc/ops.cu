@@ -1062,6 +1062,7 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
     info->relres_est = hs[S_REL];
     info->relres_true = relres_true;
     info->t_setup_ms = c->t_setup_ms;
+    info->t_fd_setup_ms = c->t_fd_setup_ms;
     info->t_solve_ms = ms;
   }
   if (status == AFI_EBREAKDOWN) set_error("MINRES breakdown (non-finite or negative norm)");

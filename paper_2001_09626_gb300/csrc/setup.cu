@@ -278,10 +278,14 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   AFI_TRY(upload(c, &c->patches, c->hp));
   std::vector<double> hctrl(prob->ctrl, prob->ctrl + xoff);
   AFI_TRY(upload(c, &c->ctrl, hctrl));
+  AFI_CUDA(cudaDeviceSynchronize());
+  const auto tf0 = std::chrono::steady_clock::now();
   AFI_TRY(fd_prepare(c));
   AFI_TRY(fd_tc_prepare(c));
   AFI_TRY(build_1d_tables(c));
   AFI_TRY(fd_tc_tables(c));
+  AFI_CUDA(cudaDeviceSynchronize());
+  c->t_fd_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
   launch(k_patch_H, NP, 256, 0, 0, c->patches, c->ctrl, D);
   AFI_LAUNCH_CHECK();
   AFI_CUDA(cudaMemcpy(c->hp.data(), c->patches, NP * sizeof(DevPatch), cudaMemcpyDeviceToHost));
@@ -494,6 +498,13 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     AFI_CUDA(cudaEventCreateWithFlags(&ej, cudaEventDisableTiming));
     c->ev_fork = ef;
     c->ev_join = ej;
+  }
+  {   // the FD work splits (tensor-core / three-pass / SIMT), part of the FD setup
+    const auto ts0 = std::chrono::steady_clock::now();
+    AFI_TRY(fd_tc_ready(c));
+    AFI_CUDA(cudaDeviceSynchronize());
+    c->t_fd_setup_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts0).count();
   }
   AFI_CUDA(cudaDeviceSynchronize());
   auto t1 = std::chrono::steady_clock::now();
