@@ -182,6 +182,19 @@ def twisted_box(grid=(8, 8, 4), p=4, nel=48, name=None):
     return _structured(name or f"twist_p{p}_nel{nel}", 3, grid, nel_cols, p, geom)
 
 
+def with_neumann(prob: Problem, faces, name=None) -> Problem:
+    """Copy of a structured problem whose outer faces `faces` (parametric face
+    indices f = 2*l + side: direction l, side 0 = lower, 1 = upper) carry the
+    natural (zero-traction) condition instead of the homogeneous Dirichlet
+    one.  Only the Dirichlet flags change."""
+    import dataclasses
+    df = prob.dirichlet_face.copy()
+    for f in faces:
+        df[:, f] = 0
+    return dataclasses.replace(prob, dirichlet_face=df,
+                               name=name or f"{prob.name}-neumann{''.join(map(str, faces))}")
+
+
 NEL_CHOICES = (12, 16, 24, 32, 48)
 P_CHOICES = (2, 3, 4, 5)
 

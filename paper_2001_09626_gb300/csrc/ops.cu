@@ -613,6 +613,9 @@ afi_status op_PS(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   // (B B^T)^{-1} B [blkdiag H^{d-2} S_hat] B^T (B B^T)^{-1} x  (Remark 1)
   double *t1 = c->ws, *t2 = c->ws + c->n_dof;
   if (c->n_c == 0) return AFI_OK;
+  // shell dofs on a natural-boundary face and on no interface have no
+  // constraint row: B^T leaves them zero, and the Schur block reads them
+  AFI_CUDA(cudaMemsetAsync(t1, 0, (size_t)c->n_dof * sizeof(double), s));
   if (c->n_shell)
     launch(k_Bt_inv, (unsigned)((c->n_shell + 255) / 256), 256, 0, s, (const int *)c->shell_dof,
            (const int *)c->bt_ptr, (const int *)c->bt_ent, (const int2 *)c->row_grp, c->n_shell, x, t1, (const double *)c->gate);

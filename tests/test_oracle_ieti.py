@@ -84,6 +84,41 @@ def test_afieti_equals_direct(which, request):
     assert (np.diff(h) <= 1e-12).all()        # MINRES residual estimate is monotone
 
 
+@pytest.mark.parametrize("name,faces", [("C2-small", (0, 1)), ("C1", (0, 1))])
+def test_neumann_faces(name, faces):
+    """Outer faces with the natural condition (the x-faces, as in the paper's
+    weak-scaling test): fewer constraint rows, the same identities, AF-IETI
+    equals the conforming direct solve, and the solution vanishes exactly on
+    the Dirichlet nodes but not on the free faces."""
+    P = W.with_neumann(W.config(name), faces)
+    s = AFIETI(P)
+    Pd = W.config(name)
+    sd = AFIETI(Pd)
+    assert s.nc < sd.nc
+    Z = s.conforming_basis()
+    assert s.nc == s.ndof - Z.shape[1]
+    f = s.load(W.body_force_coeffs(P))
+    u, lam, info = s.solve(f, tol=1e-10)
+    ud, ld = s.direct_solve(f)
+    assert np.linalg.norm(u - ud) <= 1e-7 * np.linalg.norm(ud)
+    assert np.linalg.norm(s.B @ u) <= 1e-9 * np.linalg.norm(u)
+    on_free, on_dir = [], []
+    for k in range(P.npatch):
+        g = s.geo[k]
+        for l in range(P.dim):
+            for idx in np.ndindex(*g.ns[::-1]):
+                i = idx[::-1]
+                node = int(np.ravel_multi_index(idx, g.ns[::-1]))
+                dof = s.dof(k, l, node)
+                if P.dirichlet_face[k, 2] and i[1] == 0:       # y = 0 face: Dirichlet
+                    on_dir.append(dof)
+                if not P.dirichlet_face[k, 0] and Pd.dirichlet_face[k, 0] and i[0] == 0 \
+                        and 0 < i[1] < g.ns[1] - 1:             # free x = 0 face, off the edges
+                    on_free.append(dof)
+    assert np.all(u[on_dir] == 0.0) or np.max(np.abs(u[on_dir])) <= 1e-10 * np.max(np.abs(u))
+    assert np.max(np.abs(u[on_free])) > 1e-3 * np.max(np.abs(u))
+
+
 def test_preconditioner_spd_on_subspace():
     P = W.config("C1-small")
     s = AFIETI(P)
