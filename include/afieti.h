@@ -93,10 +93,19 @@ typedef struct {
                                       used for tensors larger than one CTA
                                       (same operator; for testing and
                                       measuring that path on small patches) */
+#define AFI_VARIANT_STENCIL_F64 4  /* keep the stiffness stencil in FP64 and
+                                      apply it with FP64 FMAs.  By default each
+                                      coefficient is stored in the same 8 bytes
+                                      as a sum of two FP32 numbers (relative
+                                      error <= 2^-48) and the stiffness matvec
+                                      runs in double-FP32 arithmetic on the
+                                      FP32 pipe; its inputs and results must
+                                      then lie within the FP32 range */
 
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
- * preconditioned residual estimate and then the true FP64 residual
- * ||b - A x|| / ||b|| of eq. (4.7) must both reach it); maxit: iteration cap;
+ * preconditioned residual estimate and then the true residual
+ * ||b - A x|| / ||b|| of eq. (4.7), with the stiffness applied as set by
+ * AFI_VARIANT_STENCIL_F64, must both reach it); maxit: iteration cap;
  * use_graph: 1 runs the MINRES iterations as replays of a CUDA graph of six
  * captured iterations (same iterates and iteration count as 0, which
  * launches every kernel from the host); variant: 0 or a combination of the
@@ -123,7 +132,8 @@ typedef struct {
 } afi_info;
 
 /* Operators of the hot path, for afi_apply (each is one row of the solve):
- *  AFI_OP_STIFFNESS  y = A x                 (torn -> torn), eqs. 3.1, 4.2
+ *  AFI_OP_STIFFNESS  y = A x                 (torn -> torn), eqs. 3.1, 4.2;
+ *                    double-FP32 unless AFI_VARIANT_STENCIL_F64
  *  AFI_OP_B          y = B x                 (torn -> multipliers), Sec. 4
  *  AFI_OP_BT         y = B^T x               (multipliers -> torn)
  *  AFI_OP_PCHI       y = P_chi x             (multipliers), eq. 4.6

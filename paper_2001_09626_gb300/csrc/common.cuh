@@ -165,6 +165,8 @@ struct afi_ctx {
   unsigned char *tcpool = nullptr; long long tcpool_n = 0;   // tensor-core B operands
   double *ctrl = nullptr;                     // all control points
   double *stencil = nullptr; long long stencil_n = 0;
+  bool stencil_pairs = false;                 // stencil holds (hi, lo) FP32 pairs
+  float2 *xsplit = nullptr;                   // (hi, lo) FP32 pairs of the matvec input
   double *qgeo = nullptr; long long nqp = 0;  // [DIM*DIM + 1][nqp] SoA
 
   // constraints
@@ -229,6 +231,7 @@ void free_context(afi_ctx *c);
 
 // ops.cu (FP64 operators on the hot path)
 afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status stencil_to_pairs(afi_ctx *c);
 afi_status op_B(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status op_Bt(afi_ctx *c, const double *x, double *y, bool accumulate, bool zero_first,
                  cudaStream_t s);

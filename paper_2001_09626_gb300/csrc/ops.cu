@@ -1,6 +1,5 @@
 // FP64 operators of the AF-IETI iteration (Section 4) and the preconditioned
-// MINRES driver:
-//  * stiffness matvec y = A x from the assembled per-node stencil (eq. 4.2);
+// MINRES driver (the stiffness matvec is in stencil.cu):
 //  * jump operators B x (row gather) and B^T x (gather over the rows that
 //    touch each interface copy), (B B^T)^{-1} per geometric node (closed form
 //    of the block I + 1 1^T, Remark 1);
@@ -56,84 +55,6 @@ __device__ __forceinline__ void block_sum_multi(double *vals, int nv, double *sh
       vals[i] = v;
     }
   __syncthreads();
-}
-
-// ------------------------------------------------------- stiffness matvec
-// One thread per node: y_l(node) = sum_m sum_o A[l][m][o][node] x_m(node + o).
-// Stencil planes have rows padded to even length n1p (padding coefficients
-// are zero); x and y use the torn layout.  Consecutive threads read
-// consecutive coefficients of one plane (coalesced).
-// PC > 0: degree known at compile time (fully unrolled neighbour rows);
-// PC = 0: any degree.
-template <int DIM, int PC>
-__global__ void __launch_bounds__(128) k_stencil_mv(const DevPatch *P, const double *__restrict__ A,
-                                                    const double *__restrict__ x,
-                                                    double *__restrict__ y, const double *gate) {
-  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
-  const DevPatch pt = P[blockIdx.y];
-  const int node = blockIdx.x * blockDim.x + threadIdx.x;
-  if (node >= pt.N) return;
-  const int n1 = pt.n[0], n2 = pt.n[1], n3 = pt.n[2], p = PC > 0 ? PC : pt.p;
-  const int i1 = node % n1, i2 = (node / n1) % n2, i3 = node / (n1 * n2);
-  const int W1 = PC > 0 ? 2 * PC + 1 : pt.W[0], W2 = PC > 0 ? 2 * PC + 1 : pt.W[1];
-  const int W3 = (DIM == 3) ? W2 : 1;
-  double acc[DIM];
-#pragma unroll
-  for (int l = 0; l < DIM; ++l) acc[l] = 0.0;
-  const long long N = pt.N, S = pt.S, NP = pt.NP;
-  const double *Ab = A + pt.soff + i1 + (long long)pt.n1p * (i2 + (long long)n2 * i3);
-  for (int m = 0; m < DIM; ++m) {
-    const double *xm = x + pt.off + m * N;
-    for (int o3 = 0; o3 < W3; ++o3) {
-      const int j3 = (DIM == 3) ? i3 + o3 - p : i3;
-      if (j3 < 0 || j3 >= n3) continue;
-      for (int o2 = 0; o2 < W2; ++o2) {
-        const int j2 = i2 + o2 - p;
-        if (j2 < 0 || j2 >= n2) continue;
-        const int orow = W1 * (o2 + W2 * o3);
-        const long long jrow = (long long)n1 * (j2 + (long long)n2 * j3);
-#pragma unroll
-        for (int o1 = 0; o1 < W1; ++o1) {
-          const int j1 = i1 + o1 - p;
-          const double xv = (j1 >= 0 && j1 < n1) ? xm[jrow + j1] : 0.0;
-          const long long o = orow + o1;
-#pragma unroll
-          for (int l = 0; l < DIM; ++l) acc[l] += Ab[((long long)(l * DIM + m) * S + o) * NP] * xv;
-        }
-      }
-    }
-  }
-  for (int l = 0; l < DIM; ++l) y[pt.off + l * N + node] = acc[l];
-}
-
-afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
-  dim3 g((c->max_N + 127) / 128, c->npatch);
-  int pu = c->hp[0].p;   // one degree for every patch -> specialised kernel
-  for (auto &p : c->hp)
-    if (p.p != pu) pu = 0;
-  const double *A = c->stencil;
-  const DevPatch *P = c->patches;
-#define AFI_MV(D, PC) launch(k_stencil_mv<D, PC>, g, 128, 0, s, P, A, x, y, c->gate)
-  if (c->dim == 3) {
-    switch (pu) {
-      case 1: AFI_MV(3, 1); break;
-      case 2: AFI_MV(3, 2); break;
-      case 3: AFI_MV(3, 3); break;
-      case 4: AFI_MV(3, 4); break;
-      case 5: AFI_MV(3, 5); break;
-      default: AFI_MV(3, 0);
-    }
-  } else {
-    switch (pu) {
-      case 1: AFI_MV(2, 1); break;
-      case 2: AFI_MV(2, 2); break;
-      case 3: AFI_MV(2, 3); break;
-      default: AFI_MV(2, 0);
-    }
-  }
-#undef AFI_MV
-  AFI_LAUNCH_CHECK();
-  return AFI_OK;
 }
 
 // ------------------------------------------------------------------ jumps
