@@ -46,8 +46,10 @@ typedef enum {
 } afi_status;
 
 /* Arithmetic of the local solvers (fast diagonalization and the parametric
- * stiffness products inside the Schur preconditioner).  Everything else
- * (stiffness matvec, jumps, projectors, Krylov algebra) is FP64 always. */
+ * stiffness products inside the Schur preconditioner).  The jumps,
+ * projectors, Krylov algebra and true residual are FP64 always; the
+ * stiffness matvec of the iterations is FP64 or double-FP32, see
+ * AFI_VARIANT_STENCIL_F64. */
 typedef enum {
   AFI_FD_FP64 = 0,   /* plain form: FP64 throughout */
   AFI_FD_FP32 = 1,   /* FP32 contractions, FP32 accumulate */
@@ -93,19 +95,30 @@ typedef struct {
                                       used for tensors larger than one CTA
                                       (same operator; for testing and
                                       measuring that path on small patches) */
-#define AFI_VARIANT_STENCIL_F64 4  /* keep the stiffness stencil in FP64 and
-                                      apply it with FP64 FMAs.  By default each
-                                      coefficient is stored in the same 8 bytes
-                                      as a sum of two FP32 numbers (relative
-                                      error <= 2^-48) and the stiffness matvec
-                                      runs in double-FP32 arithmetic on the
-                                      FP32 pipe; its inputs and results must
-                                      then lie within the FP32 range */
+#define AFI_VARIANT_STENCIL_F64 4  /* apply the stiffness with FP64 FMAs
+                                      everywhere.  By default, when a second
+                                      copy of the stencil fits in device memory
+                                      (with a tenth of it to spare), each
+                                      coefficient is also stored as a sum of
+                                      two FP32 numbers (relative error <=
+                                      2^-48), and the MINRES iterations and
+                                      afi_apply(AFI_OP_STIFFNESS / SADDLE) run
+                                      the matvec in double-FP32 arithmetic on
+                                      the FP32 pipe (inputs and results within
+                                      the FP32 range); the true residual is
+                                      always FP64 */
+#define AFI_VARIANT_FORCE_RESTART 8 /* with the double-FP32 stiffness: take the
+                                      FP64 restart at the first true-residual
+                                      check, as if the iteration had stalled
+                                      (same converged answer; for testing and
+                                      timing that path) */
 
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
- * preconditioned residual estimate and then the true residual
- * ||b - A x|| / ||b|| of eq. (4.7), with the stiffness applied as set by
- * AFI_VARIANT_STENCIL_F64, must both reach it); maxit: iteration cap;
+ * preconditioned residual estimate and then the true FP64 residual
+ * ||b - A x|| / ||b|| of eq. (4.7) must both reach it; when the
+ * double-FP32 stiffness of the iterations keeps the true residual from
+ * falling, MINRES restarts once from the current iterate with the FP64
+ * stiffness, see afi_info.fp64_restarts); maxit: iteration cap;
  * use_graph: 1 runs the MINRES iterations as replays of a CUDA graph of six
  * captured iterations (same iterates and iteration count as 0, which
  * launches every kernel from the host); variant: 0 or a combination of the
@@ -119,7 +132,8 @@ typedef struct {
 } afi_options;
 
 /* Filled by ieti_solve / ieti_solve_adjoint (for the last right-hand side):
- * iterations, the MINRES estimate, the true relative residual, the setup
+ * iterations (of both runs when restarted), the MINRES estimate, the true
+ * relative residual (FP64 stiffness), the setup
  * time of the context, the wall time of this solve (device events) and the
  * part of the setup that builds the local solvers of Algorithm 1 (univariate
  * matrices, generalised eigensolves of eq. 5.8, tensor-core operand tables,
@@ -129,6 +143,7 @@ typedef struct {
   double relres_est, relres_true;
   double t_setup_ms, t_solve_ms;
   double t_fd_setup_ms;
+  int fp64_restarts;   /* 1 if the solve restarted with the FP64 stiffness */
 } afi_info;
 
 /* Operators of the hot path, for afi_apply (each is one row of the solve):
@@ -238,7 +253,8 @@ afi_status afi_fd_apply_static(int n1, int n2, int n3, const double *U1, const d
 /* n_dof (torn length) and n_c (number of constraints). */
 afi_status afi_sizes(const afi_ctx *ctx, long *n_dof, long *n_c);
 
-/* Device bytes held by the context and the stiffness storage alone. */
+/* Device bytes held by the context and the stiffness storage alone (the
+ * FP64 stencil plus its FP32-pair copy when there is one). */
 afi_status afi_memory(const afi_ctx *ctx, long long *total_bytes, long long *stiffness_bytes);
 
 void af_ieti_destroy(afi_ctx *ctx);

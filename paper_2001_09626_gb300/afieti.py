@@ -40,7 +40,7 @@ class afi_options(C.Structure):
 class afi_info(C.Structure):
     _fields_ = [("iters", C.c_int), ("relres_est", C.c_double), ("relres_true", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double),
-                ("t_fd_setup_ms", C.c_double)]
+                ("t_fd_setup_ms", C.c_double), ("fp64_restarts", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -166,6 +166,7 @@ class Problem:
 AFI_VARIANT_LOCAL_ONLY = 1
 AFI_VARIANT_FD_SLAB = 2
 AFI_VARIANT_STENCIL_F64 = 4
+AFI_VARIANT_FORCE_RESTART = 8
 
 
 def af_ieti_setup(prob, prec="fp64", tol=1e-8, maxit=2000, use_graph=False, variant=0):

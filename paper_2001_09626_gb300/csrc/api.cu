@@ -119,7 +119,7 @@ afi_status afi_sizes(const afi_ctx *c, long *n_dof, long *n_c) {
 afi_status afi_memory(const afi_ctx *c, long long *total, long long *stiff) {
   if (!c) { set_error("afi_memory: null context"); return AFI_EINVAL; }
   if (total) *total = c->bytes;
-  if (stiff) *stiff = c->stencil_n * (long long)sizeof(double);
+  if (stiff) *stiff = c->stencil_n * (long long)sizeof(double) * (c->stencil2 ? 2 : 1);
   return AFI_OK;
 }
 

@@ -115,6 +115,8 @@ struct DevPatch {
   long long off;    // torn offset of component 0
   long long ioff;   // compact interior offset of component 0
   long long soff;   // stiffness stencil offset (doubles)
+  long long roff;   // offset in the row-compressed pair copy (pairs)
+  long long rstride;  // pairs per row group of the pair copy
   long long qoff;   // quadrature geometry offset (points)
   long long xoff;   // control point offset (doubles)
   double lam, mu, Hs;  // Lame values, H^{d-2}
@@ -165,8 +167,10 @@ struct afi_ctx {
   unsigned char *tcpool = nullptr; long long tcpool_n = 0;   // tensor-core B operands
   double *ctrl = nullptr;                     // all control points
   double *stencil = nullptr; long long stencil_n = 0;
-  bool stencil_pairs = false;                 // stencil holds (hi, lo) FP32 pairs
+  float2 *stencil2 = nullptr;                 // row-compressed (hi, lo) FP32-pair copy, or null
+  long long stencil2_n = 0;                   // its size in pairs
   float2 *xsplit = nullptr;                   // (hi, lo) FP32 pairs of the matvec input
+  bool mv_exact = false;                      // apply the FP64 stencil even if pairs exist
   double *qgeo = nullptr; long long nqp = 0;  // [DIM*DIM + 1][nqp] SoA
 
   // constraints
@@ -232,6 +236,8 @@ void free_context(afi_ctx *c);
 // ops.cu (FP64 operators on the hot path)
 afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status stencil_to_pairs(afi_ctx *c);
+bool stiffness_has_pairs(const afi_ctx *c);
+long long pair_layout(std::vector<afi::DevPatch> &hp, int dim);
 afi_status op_B(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status op_Bt(afi_ctx *c, const double *x, double *y, bool accumulate, bool zero_first,
                  cudaStream_t s);

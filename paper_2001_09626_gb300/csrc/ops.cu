@@ -617,12 +617,12 @@ afi_status op_saddle(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
 // convergence (inside a replayed graph) leave the state untouched.
 enum { S_BETA1 = 0, S_BETA, S_OLDB, S_ALFA, S_DBAR, S_EPSLN, S_OLDEPS, S_PHIBAR, S_CS, S_SN,
        S_DELTA, S_GAMMA, S_PHI, S_REL, S_BETA2, S_FLAG, S_DOT, S_BNORM2, S_RES2, S_INVBETA,
-       S_BOVERO, S_INVGAMMA, S_ACTIVE, S_ITN, S_NEXTCHECK, S_MAXIT, S_COUNT };
+       S_BOVERO, S_INVGAMMA, S_ACTIVE, S_ITN, S_NEXTCHECK, S_MAXIT, S_TOL, S_COUNT };
 
 constexpr int kRelHist = 64;   // st[64 + itn % 8]: estimate of the last 8 iterations
 constexpr int kHostStats = kRelHist + 8;
 
-__global__ void k_minres_init(double *st, double maxit) {
+__global__ void k_minres_init(double *st, double maxit, double tol) {
   for (int i = 0; i < 8; ++i) st[kRelHist + i] = 1.0;
   double b2 = st[S_BETA2];
   double beta1 = (b2 >= 0.0 && isfinite(b2)) ? sqrt(b2) : -1.0;
@@ -641,6 +641,7 @@ __global__ void k_minres_init(double *st, double maxit) {
   st[S_ITN] = 0.0;
   st[S_NEXTCHECK] = 0.0;
   st[S_MAXIT] = maxit;
+  st[S_TOL] = tol;
   st[S_FLAG] = (beta1 < 0.0) ? 2.0 : (beta1 == 0.0 ? 1.0 : 0.0);
 }
 
@@ -722,8 +723,9 @@ __global__ void k_dot_active(const double *r2, const double *y, long n, double *
   grid_sum_last(s, part, counter, st + S_BETA2);
 }
 
-__global__ void k_minres_scalars(double *st, double tol) {
+__global__ void k_minres_scalars(double *st) {
   if (st[S_ACTIVE] == 0.0) return;
+  const double tol = st[S_TOL];
   double beta2 = st[S_BETA2];
   if (!(beta2 >= 0.0) || !isfinite(beta2)) { st[S_FLAG] = 2.0; return; }
   double beta = st[S_BETA], alfa = st[S_ALFA];
@@ -787,8 +789,9 @@ __global__ void k_add(const double *a, const double *b, double *out, long n) {
 static inline unsigned nblk(long n) { return (unsigned)((n + 255) / 256); }
 
 // Buffers of the iteration: three rotating Krylov vectors B (r1, r2, y), two
-// rotating search directions W, and fixed v, x and operator outputs tA, tB.
-struct MinresBufs { double *b, *x, *v, *B[3], *W[2], *tA, *tB, *tmp, *lam0; };
+// rotating search directions W, and fixed v, x, the operator output tA and
+// the iterate x0 kept across an FP64 restart.
+struct MinresBufs { double *b, *x, *v, *B[3], *W[2], *tA, *x0, *tmp, *lam0; };
 
 static MinresBufs minres_bufs(afi_ctx *c) {
   const long nt = c->n_dof + c->n_c;
@@ -797,7 +800,7 @@ static MinresBufs minres_bufs(afi_ctx *c) {
   M.b = V; M.x = V + nt; M.v = V + 2 * nt;
   M.B[0] = V + 3 * nt; M.B[1] = V + 4 * nt; M.B[2] = V + 5 * nt;
   M.W[0] = V + 6 * nt; M.W[1] = V + 7 * nt;
-  M.tA = V + 8 * nt; M.tB = V + 9 * nt; M.tmp = V + 10 * nt; M.lam0 = V + 11 * nt;
+  M.tA = V + 8 * nt; M.x0 = V + 9 * nt; M.tmp = V + 10 * nt; M.lam0 = V + 11 * nt;
   return M;
 }
 
@@ -824,7 +827,7 @@ static afi_status enqueue_iteration(afi_ctx *c, const MinresBufs &M, long t, cud
   AFI_TRY(op_precond(c, y, r1, s));
   launch(k_dot_active, kDotBlocks, 256, 0, s, (const double *)y, (const double *)r1, nt, st,
          c->small + kPart, cnt + 1);
-  launch(k_minres_scalars, 1, 1, 0, s, st, c->opt.tol);
+  launch(k_minres_scalars, 1, 1, 0, s, st);
   launch(k_w_upd, nblk(nt), 256, 0, s, M.v, (const double *)w1, (const double *)w2, w1, M.x,
          (const double *)r1, nt, (const double *)st);
   AFI_LAUNCH_CHECK();
@@ -861,16 +864,139 @@ static afi_status ensure_graph(afi_ctx *c, const MinresBufs &M) {
   return AFI_OK;
 }
 
+// The stiffness runs with FP64 products inside this scope (the true
+// residual), whatever stencil form the iterations use.
+struct ExactStiffness {
+  afi_ctx *c;
+  bool old;
+  explicit ExactStiffness(afi_ctx *cc) : c(cc), old(cc->mv_exact) { c->mv_exact = true; }
+  ~ExactStiffness() { c->mv_exact = old; }
+};
+
+// ||b - calA x||^2 with the FP64 stiffness into st[S_RES2]; hs refreshed
+static afi_status true_residual2(afi_ctx *c, const MinresBufs &M, double *hs, cudaStream_t s) {
+  const long nt = c->n_dof + c->n_c;
+  double *st = c->small;
+  {
+    ExactStiffness ex(c);
+    AFI_TRY(op_saddle(c, M.x, M.tmp, s));
+  }
+  launch(k_sub, nblk(nt), 256, 0, s, (const double *)M.b, (const double *)M.tmp, M.tmp, nt);
+  AFI_TRY(dot(c, M.tmp, M.tmp, nt, st + S_RES2, s));
+  AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AFI_CUDA(cudaStreamSynchronize(s));
+  return AFI_OK;
+}
+
+// MINRES from x = 0 on the right-hand side in M.b: r1 = r2 = b,
+// y = M^{-1} b, beta_1, ||b||^2, the recurrence scalars (estimate tolerance
+// tol_est, iteration cap maxit) and v = y / beta_1; hs refreshed
+static afi_status minres_start(afi_ctx *c, const MinresBufs &M, double tol_est, long maxit, double *hs,
+                               cudaStream_t s) {
+  const long nt = c->n_dof + c->n_c;
+  double *st = c->small;
+  AFI_CUDA(cudaMemsetAsync(M.x, 0, nt * sizeof(double), s));
+  AFI_CUDA(cudaMemsetAsync(M.W[0], 0, nt * sizeof(double), s));
+  AFI_CUDA(cudaMemsetAsync(M.W[1], 0, nt * sizeof(double), s));
+  AFI_CUDA(cudaMemcpyAsync(M.B[0], M.b, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AFI_CUDA(cudaMemcpyAsync(M.B[1], M.b, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AFI_TRY(op_precond(c, M.B[0], M.B[2], s));
+  AFI_TRY(dot(c, M.B[0], M.B[2], nt, st + S_BETA2, s));
+  AFI_TRY(dot(c, M.b, M.b, nt, st + S_BNORM2, s));
+  launch(k_minres_init, 1, 1, 0, s, st, (double)maxit, tol_est);
+  launch(k_v_from_y, nblk(nt), 256, 0, s, (const double *)M.B[2], M.v, nt, (const double *)st);
+  AFI_LAUNCH_CHECK();
+  AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
+  AFI_CUDA(cudaStreamSynchronize(s));
+  return AFI_OK;
+}
+
+struct LoopResult {
+  afi_status status = AFI_OK;
+  bool converged = false;
+  bool stalled = false;     // the true residual stopped falling (stiffness rounding floor)
+  double relres_true = 0.0;
+  long checked_at = -1;     // iteration of the last true-residual check
+};
+
+// Iterate until the estimate and the FP64 true residual (relative to bnorm)
+// both reach tol.  With stop_on_stall, return as soon as a failed check
+// shows the true residual less than halved since the previous failed check
+// while the estimate kept falling: the iteration's stiffness rounding sets
+// the floor, and the caller restarts with the FP64 stiffness.  force_stall
+// treats the first check as such a stall.
+static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, bool use_graph, double bnorm, bool stop_on_stall,
+                              bool force_stall, double *hs, cudaStream_t s) {
+  LoopResult R;
+  double *st = c->small;
+  const double tol = c->opt.tol;
+  long t = 0;   // completed iterations (buffer roles)
+  double last_fail = 0.0;
+  auto fail = [&](afi_status e) { R.status = e; return R; };
+  if (hs[S_FLAG] == 2.0) return fail(AFI_EBREAKDOWN);
+  if (hs[S_FLAG] != 0.0) { R.converged = true; }   // b = 0
+  while (!R.converged) {
+    afi_status e = AFI_OK;
+    if (use_graph && t % kGraphIters == 0) {
+      if (cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, s) != cudaSuccess) return fail(AFI_ECUDA);
+      g_launches.fetch_add(c->graph_nodes);
+      t += kGraphIters;
+    } else {
+      e = enqueue_iteration(c, M, t, s);
+      if (e != AFI_OK) return fail(e);
+      t += 1;
+    }
+    if (cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return fail(AFI_ECUDA);
+    const long itn = (long)hs[S_ITN];
+    if (hs[S_FLAG] == 2.0) return fail(AFI_EBREAKDOWN);
+    if (hs[S_FLAG] == 1.0) {
+      // estimate converged at iteration itn: confirm with the true residual
+      e = true_residual2(c, M, hs, s);
+      if (e != AFI_OK) return fail(e);
+      R.relres_true = sqrt(hs[S_RES2]) / (bnorm > 0 ? bnorm : 1.0);
+      R.checked_at = itn;
+      if (force_stall) { R.stalled = true; break; }
+      if (R.relres_true <= tol) { R.converged = true; break; }
+      if (stop_on_stall && last_fail > 0.0 && R.relres_true > 0.5 * last_fail) { R.stalled = true; break; }
+      last_fail = R.relres_true;
+      // continue from iteration itn; next check where the estimate's recent
+      // reduction rate would bring the true residual to tol (5..50 later)
+      long extra = 5;
+      if (itn >= 5) {
+        const double rn = hs[kRelHist + itn % 8], r5 = hs[kRelHist + (itn - 5) % 8];
+        if (rn > 0.0 && r5 > 0.0) {
+          const double q = pow(rn / r5, 0.2);
+          if (q > 0.0 && q < 1.0) extra = (long)ceil(log(R.relres_true / tol) / (-log(q)));
+        }
+      }
+      extra = std::min(std::max(extra, 5L), 50L);
+      launch(k_set, 1, 1, 0, s, st, (int)S_NEXTCHECK, (double)(itn + extra));
+      launch(k_set, 1, 1, 0, s, st, (int)S_FLAG, 0.0);
+      if (cudaGetLastError() != cudaSuccess) return fail(AFI_ECUDA);
+    }
+    t = itn;   // the data state corresponds to the executed iterations
+    if (itn >= (long)hs[S_MAXIT]) { R.status = AFI_ENOT_CONVERGED; break; }
+  }
+  if (R.checked_at != (long)hs[S_ITN]) {   // true residual of the final iterate
+    afi_status e = true_residual2(c, M, hs, s);
+    if (e != AFI_OK) return fail(e);
+    R.relres_true = sqrt(hs[S_RES2]) / (bnorm > 0 ? bnorm : 1.0);
+  }
+  return R;
+}
+
 // one right-hand side
 afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, afi_info *info,
                      cudaStream_t s) {
   const long n = c->n_dof, m = c->n_c, nt = n + m;
   const MinresBufs M = minres_bufs(c);
-  double *st = c->small;
   cudaEvent_t e0, e1;
   AFI_CUDA(cudaEventCreate(&e0));
   AFI_CUDA(cudaEventCreate(&e1));
   AFI_CUDA(cudaEventRecord(e0, s));
+  c->mv_exact = false;
   // lambda_0 = G (G^T G)^{-1} R^T f and b = [f - B^T lambda_0; 0]
   if (m > 0) {
     AFI_TRY(op_Rt(c, f, gbuf(c, 0), s));
@@ -882,84 +1008,41 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
     AFI_TRY(op_Bt_scaled(c, M.lam0, M.b, -1.0, true, false, s));
     AFI_CUDA(cudaMemsetAsync(M.b + n, 0, m * sizeof(double), s));
   }
-  AFI_CUDA(cudaMemsetAsync(M.x, 0, nt * sizeof(double), s));
-  AFI_CUDA(cudaMemsetAsync(M.W[0], 0, nt * sizeof(double), s));
-  AFI_CUDA(cudaMemsetAsync(M.W[1], 0, nt * sizeof(double), s));
-  // r1 = r2 = b, y = M^{-1} b
-  AFI_CUDA(cudaMemcpyAsync(M.B[0], M.b, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  AFI_CUDA(cudaMemcpyAsync(M.B[1], M.b, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  AFI_TRY(op_precond(c, M.B[0], M.B[2], s));
-  AFI_TRY(dot(c, M.B[0], M.B[2], nt, st + S_BETA2, s));
-  AFI_TRY(dot(c, M.b, M.b, nt, st + S_BNORM2, s));
-  launch(k_minres_init, 1, 1, 0, s, st, (double)c->opt.maxit);
-  launch(k_v_from_y, nblk(nt), 256, 0, s, (const double *)M.B[2], M.v, nt, (const double *)st);
-  AFI_LAUNCH_CHECK();
+  double *hs = c->host_small;
+  const double tol = c->opt.tol;
+  AFI_TRY(minres_start(c, M, tol, c->opt.maxit, hs, s));
+  const double bnorm = sqrt(hs[S_BNORM2]);
   const bool use_graph = c->opt.use_graph != 0;
   if (use_graph) {
     AFI_TRY(fd_tc_ready(c));   // no allocation or host copy during capture
     AFI_TRY(ensure_graph(c, M));
   }
-  double *hs = c->host_small;
-  AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
-  AFI_CUDA(cudaStreamSynchronize(s));
-  afi_status status = AFI_OK;
-  const double tol = c->opt.tol;
-  const double bnorm = sqrt(hs[S_BNORM2]);
-  double relres_true = 0.0;
-  long t = 0;            // completed iterations (buffer roles)
-  long checked_at = -1;  // iteration of the last true-residual check
-  if (hs[S_FLAG] == 2.0) status = AFI_EBREAKDOWN;
-  bool done = (hs[S_FLAG] != 0.0);
-  while (!done && status == AFI_OK) {
-    if (use_graph && t % kGraphIters == 0) {
-      AFI_CUDA(cudaGraphLaunch((cudaGraphExec_t)c->graph_exec, s));
-      g_launches.fetch_add(c->graph_nodes);
-      t += kGraphIters;
+  const bool pairs = stiffness_has_pairs(c);
+  LoopResult R = minres_loop(c, M, use_graph, bnorm, pairs,
+                             pairs && (c->opt.variant & AFI_VARIANT_FORCE_RESTART), hs, s);
+  long iters = (long)hs[S_ITN];
+  int restarts = 0;
+  if (R.status == AFI_OK && R.stalled) {
+    // FP64 restart from the current iterate x0: solve calA d = b - calA x0
+    // with the FP64 stiffness (host-launched iterations), then x = x0 + d
+    AFI_CUDA(cudaMemcpyAsync(M.x0, M.x, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    AFI_CUDA(cudaMemcpyAsync(M.b, M.tmp, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));   // b - calA x0
+    c->mv_exact = true;
+    const double rnorm = R.relres_true * bnorm;
+    afi_status e = minres_start(c, M, tol * bnorm / (rnorm > 0 ? rnorm : 1.0),
+                                std::max(1L, (long)c->opt.maxit - iters), hs, s);
+    if (e == AFI_OK) {
+      R = minres_loop(c, M, false, bnorm, false, false, hs, s);
+      iters += (long)hs[S_ITN];
+      restarts = 1;
     } else {
-      AFI_TRY(enqueue_iteration(c, M, t, s));
-      t += 1;
+      R.status = e;
     }
-    AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
-    AFI_CUDA(cudaStreamSynchronize(s));
-    const long itn = (long)hs[S_ITN];
-    if (hs[S_FLAG] == 2.0) { status = AFI_EBREAKDOWN; break; }
-    if (hs[S_FLAG] == 1.0) {
-      // estimate converged at iteration itn: confirm with the true residual
-      AFI_TRY(op_saddle(c, M.x, M.tmp, s));
-      launch(k_sub, nblk(nt), 256, 0, s, (const double *)M.b, (const double *)M.tmp, M.tmp, nt);
-      AFI_TRY(dot(c, M.tmp, M.tmp, nt, st + S_RES2, s));
-      AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
-      AFI_CUDA(cudaStreamSynchronize(s));
-      relres_true = sqrt(hs[S_RES2]) / (bnorm > 0 ? bnorm : 1.0);
-      checked_at = itn;
-      if (relres_true <= tol) { done = true; break; }
-      // continue from iteration itn; next check where the estimate's recent
-      // reduction rate would bring the true residual to tol (5..50 later)
-      long extra = 5;
-      if (itn >= 5) {
-        const double rn = hs[kRelHist + itn % 8], r5 = hs[kRelHist + (itn - 5) % 8];
-        if (rn > 0.0 && r5 > 0.0) {
-          const double q = pow(rn / r5, 0.2);
-          if (q > 0.0 && q < 1.0) extra = (long)ceil(log(relres_true / tol) / (-log(q)));
-        }
-      }
-      extra = std::min(std::max(extra, 5L), 50L);
-      launch(k_set, 1, 1, 0, s, st, (int)S_NEXTCHECK, (double)(itn + extra));
-      launch(k_set, 1, 1, 0, s, st, (int)S_FLAG, 0.0);
-      AFI_LAUNCH_CHECK();
-    }
-    t = itn;   // the data state corresponds to the executed iterations
-    if (itn >= c->opt.maxit) { status = AFI_ENOT_CONVERGED; break; }
+    c->mv_exact = false;
+    launch(k_add, nblk(nt), 256, 0, s, (const double *)M.x0, (const double *)M.x, M.x, nt);
+    AFI_LAUNCH_CHECK();
   }
-  const long itn_final = (long)hs[S_ITN];
-  if (checked_at != itn_final) {   // true residual of the final iterate
-    AFI_TRY(op_saddle(c, M.x, M.tmp, s));
-    launch(k_sub, nblk(nt), 256, 0, s, (const double *)M.b, (const double *)M.tmp, M.tmp, nt);
-    AFI_TRY(dot(c, M.tmp, M.tmp, nt, st + S_RES2, s));
-    AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
-    AFI_CUDA(cudaStreamSynchronize(s));
-    relres_true = sqrt(hs[S_RES2]) / (bnorm > 0 ? bnorm : 1.0);
-  }
+  afi_status status = R.status;
   // recovery: u = w - R (G^T G)^{-1} G^T B w, lambda = lambda_0 + chi
   AFI_CUDA(cudaMemcpyAsync(u, M.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (m > 0) {
@@ -974,7 +1057,7 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   }
   AFI_CUDA(cudaEventRecord(e1, s));
   AFI_CUDA(cudaEventSynchronize(e1));
-  int tc_timeout = 0;   // set by a tensor-core kernel whose bounded wait ran out
+  int tc_timeout = 0;   // set by a tensor-core or bulk-copy kernel whose bounded wait ran out
   AFI_CUDA(cudaMemcpy(&tc_timeout, c->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost));
   if (tc_timeout && status == AFI_OK) status = AFI_ETIMEOUT;
   float ms = 0.f;
@@ -982,16 +1065,17 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (info) {
-    info->iters = (int)itn_final;
+    info->iters = (int)iters;
     info->relres_est = hs[S_REL];
-    info->relres_true = relres_true;
+    info->relres_true = R.relres_true;
     info->t_setup_ms = c->t_setup_ms;
     info->t_fd_setup_ms = c->t_fd_setup_ms;
     info->t_solve_ms = ms;
+    info->fp64_restarts = restarts;
   }
   if (status == AFI_EBREAKDOWN) set_error("MINRES breakdown (non-finite or negative norm)");
   if (status == AFI_ENOT_CONVERGED) set_error("MINRES reached maxit before the tolerance");
-  if (status == AFI_ETIMEOUT) set_error("a tensor-core local solve timed out waiting for its MMAs");
+  if (status == AFI_ETIMEOUT) set_error("a tensor-core or bulk-copy kernel timed out on a bounded wait");
   return status;
 }
 

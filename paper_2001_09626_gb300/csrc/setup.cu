@@ -265,6 +265,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   c->n_int = (long)ioff;
   c->nqp = qoff;
   c->stencil_n = soff;
+  c->stencil2_n = pair_layout(c->hp, D);
   c->dpool_n = dn;
 
   // ---- device allocations for tables, patches, geometry
@@ -295,10 +296,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     AFI_TRY(dalloc(c, (void **)&c->stencil, (size_t)soff * sizeof(double)));
     AFI_CUDA(cudaMemset(c->stencil, 0, (size_t)soff * sizeof(double)));   // padded nodes stay 0
     AFI_TRY(assemble_stiffness(c));
-    if (!(opt->variant & AFI_VARIANT_STENCIL_F64)) {
-      AFI_TRY(stencil_to_pairs(c));
-      AFI_TRY(dalloc(c, (void **)&c->xsplit, (size_t)c->n_dof * sizeof(float2)));
-    }
+    if (!(opt->variant & AFI_VARIANT_STENCIL_F64)) AFI_TRY(stencil_to_pairs(c));
   } else {
     c->nqp = 0;
     c->stencil_n = 0;
@@ -532,7 +530,7 @@ void free_context(afi_ctx *c) {
                   c->tcsplit[0][0].d_line, c->tcsplit[0][1].d_plane, c->tcsplit[0][1].d_line,
                   c->tcsplit[1][0].d_plane, c->tcsplit[1][0].d_line, c->tcsplit[1][1].d_plane,
                   c->tcsplit[1][1].d_line, c->prow_coef, c->row_cp, c->row_cv, c->ps_buf,
-                  c->ps_rint, c->ps_vint, c->xsplit};
+                  c->ps_rint, c->ps_vint, c->xsplit, c->stencil2};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);

@@ -1,7 +1,8 @@
-"""The two stiffness forms (eqs. 3.1, 4.2) against the oracle: the default
-double-FP32 stencil (each coefficient and input held as a sum of two FP32
-numbers, products summed with exact product errors and TwoSum) and the FP64
-stencil of AFI_VARIANT_STENCIL_F64.
+"""The two stiffness forms (eqs. 3.1, 4.2) against the oracle: the
+iterations' double-FP32 form (a row-compressed copy of the stencil with each
+coefficient and input held as a sum of two FP32 numbers, products summed with
+exact product errors and TwoSum) and the FP64 stencil, which the true residual
+and AFI_VARIANT_STENCIL_F64 use.
 
 Element-wise bound for the double-FP32 form, with u = 2^-24 and N the number
 of products in a row: splitting a and x costs at most u^2 (|a| |x|) each, the
@@ -18,7 +19,18 @@ from oracle.ieti import AFIETI
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-CASES = ["C1", "C2-small", "C5-small"]
+# configurations, plus uneven patches of degree 5 and 2 (rows of several
+# lengths per tile, the largest neighbour stencil)
+MAKERS = {
+    "C1": lambda: W.config("C1"),
+    "C2-small": lambda: W.config("C2-small"),
+    "C5-small": lambda: W.config("C5-small"),
+    "annulus-p5-uneven": lambda: W.quarter_annulus(grid=(2, 1, 1), p=5, nel_cols=[[3, 5], [4], [3]],
+                                                   name="annulus-p5-uneven"),
+    "annulus-p2-uneven": lambda: W.quarter_annulus(grid=(2, 1, 2), p=2, nel_cols=[[6, 3], [5], [2, 7]],
+                                                   name="annulus-p2-uneven"),
+}
+CASES = list(MAKERS)
 
 
 def nprod(prob):
@@ -36,7 +48,7 @@ def pair(request):
     import __graft_entry__ as g
     g.build()
     from paper_2001_09626_gb300.solver import Solver
-    prob = W.config(request.param)
+    prob = MAKERS[request.param]()
     orc = AFIETI(prob)
     orc.assemble()
     sd = Solver(prob, prec="fp64", tol=1e-10)
@@ -93,14 +105,36 @@ def test_solves_agree(pair, prec):
             assert s.last_info["relres_true"] <= 1e-10
             assert np.linalg.norm(u.cpu().numpy() - ud) <= 1e-7 * np.linalg.norm(ud)
             its.append(s.last_info["iters"])
+            assert s.last_info["fp64_restarts"] == 0
         finally:
             s.set_precision("fp64")
-    # the forms differ by rounding only: the stopping iteration may move by
-    # one period (5 iterations) of the true-residual check schedule
-    assert abs(its[0] - its[1]) <= 5, its
+    # the forms differ by rounding only: the stopping iteration may move by a
+    # period of the true-residual check schedule (5 or more iterations)
+    assert abs(its[0] - its[1]) <= max(5, 0.03 * max(its)), its
 
 
-def test_memory_is_unchanged(pair):
+def test_memory_of_the_pair_copy(pair):
     from paper_2001_09626_gb300 import afieti as A
     _, _, _, sd, s64 = pair
-    assert A.afi_memory(sd.ctx)[1] == A.afi_memory(s64.ctx)[1]
+    assert A.afi_memory(sd.ctx)[1] == 2 * A.afi_memory(s64.ctx)[1]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32"])
+def test_fp64_restart(pair, prec):
+    """The restart a stalled double-FP32 iteration takes (forced here at the
+    first true-residual check): MINRES continues from the iterate with the
+    FP64 stiffness on b - calA x0 and returns x0 + d, the same solution."""
+    from paper_2001_09626_gb300.solver import Solver
+    name, prob, orc, sd, _ = pair
+    f = orc.load(W.body_force_coeffs(prob))
+    ud, ld = orc.direct_solve(f)
+    sr = Solver(prob, prec=prec, tol=1e-10, force_restart=True)
+    try:
+        u, lam = sr.solve(T(f))
+        info = sr.last_info
+        assert info["fp64_restarts"] == 1
+        assert info["relres_true"] <= 1e-10
+        assert np.linalg.norm(u.cpu().numpy() - ud) <= 1e-7 * np.linalg.norm(ud)
+        assert np.linalg.norm(lam.cpu().numpy() - ld) <= 1e-7 * np.linalg.norm(ld)
+    finally:
+        sr.close()
