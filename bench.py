@@ -387,6 +387,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (10.8 GB stencil streamed each iteration)"},
             "iterations": info["iters"], "relres_true": info["relres_true"],
+            "fp64_restarts": info["fp64_restarts"],
             "setup_s": round(setup_s, 3),
             "solve_s_without_fd_setup": round(ms_solve / 1e3, 4),
             "fd_setup_s": round(fd_setup_ms / 1e3, 4),

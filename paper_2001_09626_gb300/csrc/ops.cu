@@ -921,9 +921,9 @@ struct LoopResult {
 
 // Iterate until the estimate and the FP64 true residual (relative to bnorm)
 // both reach tol.  With stop_on_stall, return as soon as a failed check
-// shows the true residual less than halved since the previous failed check
-// while the estimate kept falling: the iteration's stiffness rounding sets
-// the floor, and the caller restarts with the FP64 stiffness.  force_stall
+// shows the true residual nearly flat since the previous failed check while
+// the estimate kept falling: the iteration's stiffness rounding then sets a
+// floor, and the caller restarts with the FP64 stiffness.  force_stall
 // treats the first check as such a stall.
 static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, bool use_graph, double bnorm, bool stop_on_stall,
                               bool force_stall, double *hs, cudaStream_t s) {
@@ -931,7 +931,7 @@ static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, bool use_graph, d
   double *st = c->small;
   const double tol = c->opt.tol;
   long t = 0;   // completed iterations (buffer roles)
-  double last_fail = 0.0;
+  double last_fail = 0.0, last_est = 0.0;   // true residual and estimate at the last failed check
   auto fail = [&](afi_status e) { R.status = e; return R; };
   if (hs[S_FLAG] == 2.0) return fail(AFI_EBREAKDOWN);
   if (hs[S_FLAG] != 0.0) { R.converged = true; }   // b = 0
@@ -959,8 +959,15 @@ static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, bool use_graph, d
       R.checked_at = itn;
       if (force_stall) { R.stalled = true; break; }
       if (R.relres_true <= tol) { R.converged = true; break; }
-      if (stop_on_stall && last_fail > 0.0 && R.relres_true > 0.5 * last_fail) { R.stalled = true; break; }
+      // stall: since the previous failed check the estimate has fallen by
+      // more than 4x while the true residual fell by less than 1.5x
+      const double est = hs[S_REL];
+      if (stop_on_stall && last_fail > 0.0 && est < 0.25 * last_est && R.relres_true > last_fail / 1.5) {
+        R.stalled = true;
+        break;
+      }
       last_fail = R.relres_true;
+      last_est = est;
       // continue from iteration itn; next check where the estimate's recent
       // reduction rate would bring the true residual to tol (5..50 later)
       long extra = 5;
