@@ -107,6 +107,18 @@ typedef struct {
                                       the FP32 pipe (inputs and results within
                                       the FP32 range); the true residual is
                                       always FP64 */
+#define AFI_VARIANT_EXACT 16       /* EXACT local solvers (Section 5.1), the
+                                      paper's iteration-count reference:
+                                      P_A^ex = A^(k) + H_k^{-2} M^(k) (eq. 5.1)
+                                      and P_S^{ex-nr} with the Schur
+                                      complements S^(k) of A^(k) (Remark 1),
+                                      applied with dense per-patch FP64
+                                      inverses built at setup; every patch
+                                      must have d N^(k) <= 4096 (else
+                                      AFI_EINVAL).  afi_apply's AFI_OP_PA_INV
+                                      and AFI_OP_SCHUR then apply these;
+                                      fd_apply stays the FD of Algorithm 1,
+                                      and afi_options.prec has no effect */
 #define AFI_VARIANT_FORCE_RESTART 8 /* with the double-FP32 stiffness: take the
                                       FP64 restart at the first true-residual
                                       check, as if the iteration had stalled
@@ -154,7 +166,9 @@ typedef struct {
  *  AFI_OP_PCHI       y = P_chi x             (multipliers), eq. 4.6
  *  AFI_OP_PU         y = P_u x               (torn), Sec. 4 after eq. 4.9
  *  AFI_OP_PA_INV     y = P_A^{-1} x          (torn), eq. 5.6 by Algorithm 1
- *  AFI_OP_SCHUR      y = blkdiag H^{d-2} S_hat x (torn shell -> torn shell),
+ *                    (AFI_VARIANT_EXACT: (A + D_H M)^{-1} x, eq. 5.1)
+ *  AFI_OP_SCHUR      y = blkdiag H^{d-2} S_hat x (torn shell -> torn shell)
+ *                    (AFI_VARIANT_EXACT: blkdiag S x, Section 5.1),
  *                    eqs. 5.4-5.5; interior entries of y are written as zero
  *  AFI_OP_PS         y = (B B^T)^{-1} B S_hat_H B^T (B B^T)^{-1} x  (Remark 1)
  *  AFI_OP_PRECOND    y = calB^{-1} x         ([torn; multipliers]), eq. 4.9

@@ -1,6 +1,6 @@
 """All-Floating IETI (Section 4) with the inexact local solvers of Section 5.2
-and the non-redundant Schur preconditioner of Remark 1, plus the conforming
-direct solve that defines the exact answer.  Oracle code: test infrastructure
+(or the exact ones of Section 5.1) and the non-redundant Schur preconditioner
+of Remark 1, plus the conforming direct solve that defines the exact answer.  Oracle code: test infrastructure
 only.
 
 Readings where the paper is silent (each listed in the design notes):
@@ -222,8 +222,64 @@ class AFIETI:
         y = self.B @ self.S_hat_H(self.B.T @ y)
         return self.BBt_lu.solve(y)
 
+    # ------------------------------------------------ exact local solvers
+    def _exact(self):
+        """Per patch (Section 5.1): the factorised P_A^ex = A^(k) + H_k^{-2} M^(k)
+        (eq. 5.1 with D_H = H^{-2} I, the scalar mass on every component) and the
+        factorised interior block A^(k)_II of the elasticity matrix (all
+        components coupled), for the exact Schur complement S^(k)."""
+        if hasattr(self, "_exa"):
+            return self._exa
+        A = self.assemble()
+        out = []
+        for k, g in enumerate(self.geo):
+            sl = slice(self.off[k], self.off[k + 1])
+            Ak = A[sl][:, sl].tocsc()
+            Mk, _ = assembly.mass_block(g)
+            Md = sp.block_diag([sp.csr_matrix(Mk)] * self.dim)
+            PA = spla.splu((Ak + Md / self.H[k] ** 2).tocsc())
+            mask = np.tile(fd.interior_mask(g.ns), self.dim)
+            AII = spla.splu(Ak[mask][:, mask].tocsc())
+            out.append((PA, Ak.tocsr(), AII, mask))
+        self._exa = out
+        return out
+
+    def PA_inv_exact(self, r):
+        """blkdiag_k (A^(k) + H_k^{-2} M^(k))^{-1} r by sparse LU (eq. 5.1)."""
+        out = np.empty_like(r)
+        for k, (PA, _, _, _) in enumerate(self._exact()):
+            sl = slice(self.off[k], self.off[k + 1])
+            out[sl] = PA.solve(r[sl])
+        return out
+
+    def S_exact(self, t):
+        """blkdiag_k S^(k) on a torn vector supported on the shell: the Schur
+        complement of A^(k) on its interface dofs, S theta = (A v)_Gamma with
+        v_Gamma = theta and v_I = -A_II^{-1} (A v^0)_I (Section 5.1)."""
+        out = np.zeros_like(t)
+        for k, (_, Ak, AII, mask) in enumerate(self._exact()):
+            sl = slice(self.off[k], self.off[k + 1])
+            v = np.where(mask, 0.0, t[sl])
+            y = Ak @ v
+            v[mask] = -AII.solve(y[mask])
+            z = Ak @ v
+            out[sl] = np.where(mask, 0.0, z)
+        return out
+
+    def P_S_exact(self, x):
+        """P_S^{ex-nr} = (B B^T)^{-1} B S B^T (B B^T)^{-1} (Remark 1)."""
+        y = self.BBt_lu.solve(x)
+        y = self.B @ self.S_exact(self.B.T @ y)
+        return self.BBt_lu.solve(y)
+
     def precond_apply(self, rw, rc):
-        """B^{-1} of eq. 4.9: blkdiag(P_u P_A^{-1} P_u^T, P_chi P_S P_chi^T)."""
+        """B^{-1} of eq. 4.9: blkdiag(P_u P_A^{-1} P_u^T, P_chi P_S P_chi^T), with
+        the inexact local solvers (Section 5.2) or, for precond="exact", the
+        exact ones (Section 5.1)."""
+        if self.precond == "exact":
+            zw = self.P_u(self.PA_inv_exact(self.P_u(rw)))
+            zc = self.P_chi(self.P_S_exact(self.P_chi(rc)))
+            return zw, zc
         zw = self.P_u(self.PA_inv(self.P_u(rw)))
         zc = self.P_chi(self.P_S(self.P_chi(rc)))
         return zw, zc

@@ -94,8 +94,8 @@ afi_status afi_apply(afi_ctx *c, afi_operator op, const double *x, double *y, vo
     case AFI_OP_BT: return op_Bt(c, x, y, false, true, s);
     case AFI_OP_PCHI: return op_Pchi(c, x, y, s);
     case AFI_OP_PU: return op_Pu(c, x, y, s);
-    case AFI_OP_PA_INV: return fd_run(c, 0, x, y, s);
-    case AFI_OP_SCHUR: return schur_run(c, x, y, s);
+    case AFI_OP_PA_INV: return c->exact ? exact_PA_inv(c, x, y, s) : fd_run(c, 0, x, y, s);
+    case AFI_OP_SCHUR: return c->exact ? exact_schur(c, x, y, s) : schur_run(c, x, y, s);
     case AFI_OP_PS: return op_PS(c, x, y, s);
     case AFI_OP_PRECOND: return op_precond(c, x, y, s);
     case AFI_OP_SADDLE: return op_saddle(c, x, y, s);

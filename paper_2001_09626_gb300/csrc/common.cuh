@@ -120,6 +120,7 @@ struct DevPatch {
   long long qoff;   // quadrature geometry offset (points)
   long long xoff;   // control point offset (doubles)
   double lam, mu, Hs;  // Lame values, H^{d-2}
+  double H;            // patch diameter H^(k)
 };
 
 // Split of the patches between the tensor-core FD (tensors that fit one CTA)
@@ -170,6 +171,10 @@ struct afi_ctx {
   float2 *stencil2 = nullptr;                 // row-compressed (hi, lo) FP32-pair copy, or null
   long long stencil2_n = 0;                   // its size in pairs
   float2 *xsplit = nullptr;                   // (hi, lo) FP32 pairs of the matvec input
+  // EXACT local solvers (AFI_VARIANT_EXACT): dense per-patch inverses
+  bool exact = false;
+  double *ex_Kinv = nullptr, *ex_AIIinv = nullptr;   // (A + H^-2 M)^{-1}, A_II^{-1}
+  long long *ex_koff = nullptr, *ex_aoff = nullptr;  // their per-patch offsets
   bool mv_exact = false;                      // apply the FP64 stencil even if pairs exist
   double *qgeo = nullptr; long long nqp = 0;  // [DIM*DIM + 1][nqp] SoA
 
@@ -237,6 +242,11 @@ void free_context(afi_ctx *c);
 afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status stencil_to_pairs(afi_ctx *c);
 bool stiffness_has_pairs(const afi_ctx *c);
+afi_status op_stiffness_fp64(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+// exact.cu (EXACT local solvers, Section 5.1)
+afi_status exact_setup(afi_ctx *c);
+afi_status exact_PA_inv(afi_ctx *c, const double *r, double *s, cudaStream_t st);
+afi_status exact_schur(afi_ctx *c, const double *t, double *y, cudaStream_t st);
 long long pair_layout(std::vector<afi::DevPatch> &hp, int dim);
 afi_status op_B(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status op_Bt(afi_ctx *c, const double *x, double *y, bool accumulate, bool zero_first,

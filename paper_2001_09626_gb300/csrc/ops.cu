@@ -540,7 +540,8 @@ afi_status op_PS(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->n_shell)
     launch(k_Bt_inv, (unsigned)((c->n_shell + 255) / 256), 256, 0, s, (const int *)c->shell_dof,
            (const int *)c->bt_ptr, (const int *)c->bt_ent, (const int2 *)c->row_grp, c->n_shell, x, t1, (const double *)c->gate);
-  AFI_TRY(schur_run(c, t1, t2, s));
+  if (c->exact) AFI_TRY(exact_schur(c, t1, t2, s));
+  else AFI_TRY(schur_run(c, t1, t2, s));
   launch(k_B_inv, (unsigned)((c->n_c + 255) / 256), 256, 0, s, (const int2 *)c->row_copy,
          (const int2 *)c->row_grp, c->n_c, (const double *)t2, y, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
@@ -568,7 +569,7 @@ static afi_status join_aux(afi_ctx *c, cudaStream_t s, cudaStream_t aux) {
 // the interior tensors) may run beside the primal one (FD on the full
 // tensors) unless both local solves would use the local-solver scratch slab.
 static bool precond_branches_independent(afi_ctx *c) {
-  return !(fd_uses_scratch(c, 0) && fd_uses_scratch(c, 1));
+  return c->exact || !(fd_uses_scratch(c, 0) && fd_uses_scratch(c, 1));
 }
 
 afi_status op_precond(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
@@ -585,7 +586,8 @@ afi_status op_precond(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
     AFI_TRY(op_Pchi(c, y + n, y + n, a));
   }
   AFI_TRY(op_Pu(c, x, t1, s));
-  AFI_TRY(fd_run(c, 0, t1, y, s));
+  if (c->exact) AFI_TRY(exact_PA_inv(c, t1, y, s));
+  else AFI_TRY(fd_run(c, 0, t1, y, s));
   AFI_TRY(op_Pu(c, y, y, s));
   if (two) AFI_TRY(join_aux(c, s, a));
   return AFI_OK;

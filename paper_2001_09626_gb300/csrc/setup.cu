@@ -81,6 +81,7 @@ __global__ void k_patch_H(DevPatch *P, const double *ctrl, int dim) {
     double s2 = 0.0;
     for (int d = 0; d < dim; ++d) s2 += (hi[d][0] - lo[d][0]) * (hi[d][0] - lo[d][0]);
     double H = sqrt(s2);
+    P[k].H = H;
     P[k].Hs = (dim == 3) ? H : 1.0;
   }
 }
@@ -508,6 +509,12 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     c->t_fd_setup_ms +=
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts0).count();
   }
+  if (opt->variant & AFI_VARIANT_EXACT) {   // exact local solvers: also local-solver setup
+    const auto ts0 = std::chrono::steady_clock::now();
+    AFI_TRY(exact_setup(c));
+    c->t_fd_setup_ms +=
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - ts0).count();
+  }
   AFI_CUDA(cudaDeviceSynchronize());
   auto t1 = std::chrono::steady_clock::now();
   c->t_setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -530,7 +537,8 @@ void free_context(afi_ctx *c) {
                   c->tcsplit[0][0].d_line, c->tcsplit[0][1].d_plane, c->tcsplit[0][1].d_line,
                   c->tcsplit[1][0].d_plane, c->tcsplit[1][0].d_line, c->tcsplit[1][1].d_plane,
                   c->tcsplit[1][1].d_line, c->prow_coef, c->row_cp, c->row_cv, c->ps_buf,
-                  c->ps_rint, c->ps_vint, c->xsplit, c->stencil2};
+                  c->ps_rint, c->ps_vint, c->xsplit, c->stencil2, c->ex_Kinv, c->ex_AIIinv,
+                  c->ex_koff, c->ex_aoff};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);

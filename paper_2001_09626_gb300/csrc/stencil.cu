@@ -450,6 +450,14 @@ afi_status stencil_to_pairs(afi_ctx *c) {
 
 bool stiffness_has_pairs(const afi_ctx *c) { return c->stencil2 != nullptr; }
 
+afi_status op_stiffness_fp64(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
+  const bool old = c->mv_exact;
+  c->mv_exact = true;
+  const afi_status st = op_stiffness(c, x, y, s);
+  c->mv_exact = old;
+  return st;
+}
+
 afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->stencil2 && !c->mv_exact) {
     afi_status st = AFI_OK;
