@@ -374,7 +374,7 @@ def run_ours(args):
     gbs = alg_bytes / (mv_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(gbs / hbm, 3), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "traffic": traffic_record("k_stencil_mv_rows"),
+                "traffic": traffic_record("k_stencil_mv_rows") if args.workload == "C2" else None,
                 "kernel": "k_split_x + k_stencil_mv_rows<3,3> (double-FP32 stiffness matvec on the "
                           "row-compressed pair copy, bulk-copy pipeline)",
                 "bytes_per_launch": alg_bytes, "launch_ms": round(mv_ms, 4),
@@ -391,7 +391,8 @@ def run_ours(args):
                    "achieved": round(fd_bytes / (fd_ms[args.prec] * 1e-3) / 1e9, 1),
                    "peak": hbm, "unit": "GB/s",
                    "frac": round(fd_bytes / (fd_ms[args.prec] * 1e-3) / 1e9 / hbm, 4),
-                   "traffic": traffic_record("k_fd_tc" if args.prec in ("tf32", "bf16") else "k_fd"),
+                   "traffic": (traffic_record("k_fd_tc" if args.prec in ("tf32", "bf16") else "k_fd")
+                               if args.workload == "C2" else None),
                    "bytes_per_launch": fd_bytes,
                    "nrhs8": {"achieved": round(8 * fd_bytes / (fd8_ms[args.prec] * 1e-3) / 1e9, 1),
                              "frac": round(8 * fd_bytes / (fd8_ms[args.prec] * 1e-3) / 1e9 / hbm, 4),
@@ -401,10 +402,12 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_dof": s.n_dof, "n_c": s.n_c,
+            "config": {"workload": WORKLOAD if args.workload == "C2" else f"{args.workload} ({prob.name})",
+                       "n_dof": s.n_dof, "n_c": s.n_c,
                        "local_solver_precision": args.prec,
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (10.8 GB stencil streamed each iteration)"},
+                       "l2": f"inputs larger than L2 ({pair_copy_bytes(prob) / 1e9:.1f} GB pair stencil "
+                             "streamed each iteration)"},
             "iterations": info["iters"], "relres_true": info["relres_true"],
             "fp64_restarts": info["fp64_restarts"],
             "setup_s": round(setup_s, 3),
