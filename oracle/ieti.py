@@ -272,10 +272,55 @@ class AFIETI:
         y = self.B @ self.S_exact(self.B.T @ y)
         return self.BBt_lu.solve(y)
 
+    # --------------------------------------- geometry-inclusion local solvers
+    def _geo(self):
+        """Per patch, the geometry-inclusion blocks of Section 5.2.3 (oracle/geo.py)."""
+        if hasattr(self, "_geol"):
+            return self._geol
+        from . import geo
+        A = self.assemble()
+        out = []
+        for k, g in enumerate(self.geo):
+            sl = slice(self.off[k], self.off[k + 1])
+            Mk, _ = assembly.mass_block(g)
+            lam, mu = self.prob.lame[k]
+            out.append(geo.GeoLocal(g, lam, mu, self.H[k], A[sl][:, sl].tocsr(), Mk))
+        self._geol = out
+        return out
+
+    def PA_inv_geo(self, r):
+        """blkdiag_{k,l} (P~_A^{inex,(k)})^{-1} r (eq. 5.12)."""
+        out = np.empty_like(r)
+        for k, gl in enumerate(self._geo()):
+            for l in range(self.dim):
+                sl = slice(self.dof(k, l, 0), self.dof(k, l, 0) + self.N[k])
+                out[sl] = gl.PA_inv(l, r[sl])
+        return out
+
+    def S_geo(self, t):
+        """blkdiag_{k,l} D_S^{1/2} S~_l D_S^{1/2} on a shell-supported torn vector (eq. 5.13)."""
+        out = np.zeros_like(t)
+        for k, gl in enumerate(self._geo()):
+            for l in range(self.dim):
+                sl = slice(self.dof(k, l, 0), self.dof(k, l, 0) + self.N[k])
+                out[sl] = gl.S(l, t[sl])
+        return out
+
+    def P_S_geo(self, x):
+        """P~_S^{inex-nr} = (B B^T)^{-1} B S~ B^T (B B^T)^{-1} (Remark 1)."""
+        y = self.BBt_lu.solve(x)
+        y = self.B @ self.S_geo(self.B.T @ y)
+        return self.BBt_lu.solve(y)
+
     def precond_apply(self, rw, rc):
         """B^{-1} of eq. 4.9: blkdiag(P_u P_A^{-1} P_u^T, P_chi P_S P_chi^T), with
-        the inexact local solvers (Section 5.2) or, for precond="exact", the
-        exact ones (Section 5.1)."""
+        the inexact local solvers (Section 5.2), or for precond="exact" the exact
+        ones (Section 5.1), or for precond="geo" the geometry-inclusion ones
+        (Section 5.2.3)."""
+        if self.precond == "geo":
+            zw = self.P_u(self.PA_inv_geo(self.P_u(rw)))
+            zc = self.P_chi(self.P_S_geo(self.P_chi(rc)))
+            return zw, zc
         if self.precond == "exact":
             zw = self.P_u(self.PA_inv_exact(self.P_u(rw)))
             zc = self.P_chi(self.P_S_exact(self.P_chi(rc)))
