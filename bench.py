@@ -174,6 +174,38 @@ def oracle_sample_time(steps=1, warmup=0):
                          "sample_s": round(per, 3), "cores": _CORES}
 
 
+def oracle_fd_rate(workload="C2", max_tensors=12, seconds=3.0):
+    """The CPU oracle's FD apply (Algorithm 1 by tensordot, FP64, the host's
+    BLAS threads) on a bounded sample of the workload's (patch, component)
+    tensors: DoF/s of P_A^{-1}, the same quantity as fd_apply_dofs_per_s."""
+    import numpy as np
+    import afi_workloads as W
+    from oracle import fd as ofd
+    P = W.config(workload)
+    tensors = []
+    for k in range(min(P.npatch, max_tensors)):
+        p = int(P.degree[k])
+        Ks, Ms = ofd.patch_1d(P.nel[k], p)
+        U = [ofd.gen_eig(K, M)[1] for K, M in zip(Ks, Ms)]
+        D = [ofd.gen_eig(K, M)[0] for K, M in zip(Ks, Ms)]
+        lam, mu = P.lame[k]
+        diag = ofd.Lambda(D, P.dim, 0, lam, mu, 1.0)
+        r = np.random.default_rng(k).standard_normal(diag.shape)
+        tensors.append((r, U, diag))
+    dofs, t0, reps = 0, time.time(), 0
+    while True:
+        for r, U, diag in tensors:
+            ofd.fd_solve(r, U, diag)
+            dofs += r.size
+        reps += 1
+        if time.time() - t0 >= seconds:
+            break
+    el = time.time() - t0
+    return {"value": round(dofs / el, 1), "unit": "DoF/s", "cores": _CORES, "kind": "oracle",
+            "sample": f"{workload}: P_A^-1 FD (tensordot, FP64) on {len(tensors)} patch tensors, "
+                      f"{reps} sweeps in {el:.1f} s"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -431,6 +463,7 @@ def run_ours(args):
         val, det = oracle_sample_time(steps=1, warmup=0)
         line["cpu_baseline"] = {"value": round(val, 3), "unit": "s", "cores": det["cores"],
                                 "kind": "oracle", "sample": det["sample"]}
+        line["cpu_baseline_fd"] = oracle_fd_rate(args.workload)
     if rank == 0:
         print(json.dumps(line), flush=True)
     s.close()
@@ -495,6 +528,8 @@ def run_fd_only(args):
     line = {"metric": "FD-apply DoF/s", "unit": "DoF/s", "workload": args.workload,
             "path": "three-pass (forced)" if args.fd_slab else "automatic",
             "n_dof": s.n_dof, "n_int": n_int, "hbm_peak_GBs": hbm, "fd": out}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_fd_rate(args.workload)
     print(json.dumps(line), flush=True)
     s.close()
 
