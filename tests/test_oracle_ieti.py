@@ -236,3 +236,37 @@ def test_exact_local_solvers():
         ud, ld = se.direct_solve(f)
         assert np.linalg.norm(u - ud) <= 1e-7 * np.linalg.norm(ud)
         assert info["iters"] < info_i["iters"]
+
+
+def test_inexact_schur_pins():
+    """eqs. 5.4-5.5, 5.7: S_hat by harmonic extension equals the dense Schur
+    complement H^{d-2} (A_GG - A_GI A_II^{-1} A_IG) of the parametric A_hat_l,
+    maps constant shell vectors to zero (A_hat has the constants in its kernel),
+    and P_S is symmetric positive semi-definite."""
+    from oracle import fd as ofd
+    for name in ("C1-small", "C2-small"):
+        P = W.config(name)
+        s = AFIETI(P)
+        rng = np.random.default_rng(51)
+        for k, g in enumerate(s.geo[:2]):
+            lam, mu = P.lame[k]
+            Ks, Ms = ofd.patch_1d(g.nel, g.p)
+            inner = ofd.interior_mask(g.ns)
+            G, I = ~inner, inner
+            Hs = s.H[k] ** (s.dim - 2)
+            for l in range(s.dim):
+                Ah = ofd.A_hat(Ks, Ms, s.dim, l, lam, mu)
+                Sd = Hs * (Ah[np.ix_(G, G)] - Ah[np.ix_(G, I)] @ np.linalg.solve(Ah[np.ix_(I, I)], Ah[np.ix_(I, G)]))
+                t = np.zeros(s.ndof)
+                base = s.dof(k, l, 0)
+                tk = rng.standard_normal(int(G.sum()))
+                t[base + np.nonzero(G)[0]] = tk
+                y = s.S_hat_H(t)[base:base + s.N[k]]
+                np.testing.assert_allclose(y[G], Sd @ tk, rtol=1e-9, atol=1e-11 * np.abs(Sd).max())
+                assert not y[I].any()
+                one = np.zeros(s.ndof)
+                one[base + np.nonzero(G)[0]] = 1.0
+                assert np.abs(s.S_hat_H(one)).max() <= 1e-11 * np.abs(Sd).max()
+        x, y = rng.standard_normal(s.nc), rng.standard_normal(s.nc)
+        assert abs(x @ s.P_S(y) - y @ s.P_S(x)) <= 1e-10 * np.linalg.norm(x) * np.linalg.norm(s.P_S(y))
+        assert x @ s.P_S(x) >= -1e-12 * np.linalg.norm(x) ** 2
