@@ -96,17 +96,25 @@ typedef struct {
                                       (same operator; for testing and
                                       measuring that path on small patches) */
 #define AFI_VARIANT_STENCIL_F64 4  /* apply the stiffness with FP64 FMAs
-                                      everywhere.  By default, when a second
-                                      copy of the stencil fits in device memory
-                                      (with a tenth of it to spare), each
-                                      coefficient is also stored as a sum of
-                                      two FP32 numbers (relative error <=
-                                      2^-48), and the MINRES iterations and
+                                      everywhere.  By default, when every patch
+                                      has one degree (at most 5 in 3D, 3 in
+                                      2D) and rows of at most 128 nodes, and a
+                                      second, row-compressed copy of the
+                                      stencil fits in device memory (with a
+                                      tenth of it to spare), each coefficient
+                                      is also stored as a sum of two FP32
+                                      numbers (relative error <= 2^-48), and
+                                      the MINRES iterations and
                                       afi_apply(AFI_OP_STIFFNESS / SADDLE) run
                                       the matvec in double-FP32 arithmetic on
                                       the FP32 pipe (inputs and results within
                                       the FP32 range); the true residual is
                                       always FP64 */
+#define AFI_VARIANT_FORCE_RESTART 8 /* with the double-FP32 stiffness: take the
+                                      FP64 restart at the first true-residual
+                                      check, as if the iteration had stalled
+                                      (same converged answer; for testing and
+                                      timing that path) */
 #define AFI_VARIANT_EXACT 16       /* EXACT local solvers (Section 5.1), the
                                       paper's iteration-count reference:
                                       P_A^ex = A^(k) + H_k^{-2} M^(k) (eq. 5.1)
@@ -119,11 +127,6 @@ typedef struct {
                                       and AFI_OP_SCHUR then apply these;
                                       fd_apply stays the FD of Algorithm 1,
                                       and afi_options.prec has no effect */
-#define AFI_VARIANT_FORCE_RESTART 8 /* with the double-FP32 stiffness: take the
-                                      FP64 restart at the first true-residual
-                                      check, as if the iteration had stalled
-                                      (same converged answer; for testing and
-                                      timing that path) */
 
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
  * preconditioned residual estimate and then the true FP64 residual
