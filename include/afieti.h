@@ -42,7 +42,9 @@ typedef enum {
   AFI_ESINGULAR = 4,       /* G^T G or a pencil is not positive definite */
   AFI_ENOT_CONVERGED = 5,  /* maxit reached before the tolerance */
   AFI_EBREAKDOWN = 6,      /* MINRES breakdown (non-finite or negative norm) */
-  AFI_ETIMEOUT = 7
+  AFI_ETIMEOUT = 7         /* a bounded mbarrier wait of a tensor-core or bulk-copy
+                              kernel ran out; reported by ieti_solve and
+                              ieti_solve_adjoint at the end of the solve */
 } afi_status;
 
 /* Arithmetic of the local solvers (fast diagonalization and the parametric
@@ -286,10 +288,11 @@ const char *afi_last_error(void);
 long long afi_kernel_launches(void);
 
 /* Self-test of the library's failure path for tensor-core waits (no
- * counterpart in the paper).  Every tcgen05 kernel waits on mbarriers (TMA
- * and MMA completion) with a bounded number of polls; when a wait runs out
- * the kernel frees its tensor memory, returns, and the operation reports
- * AFI_ETIMEOUT instead of hanging the GPU.  This entry point runs that path
+ * counterpart in the paper).  Every tcgen05 and bulk-copy kernel waits on
+ * mbarriers (TMA and MMA completion) with a bounded number of polls; when a
+ * wait runs out the kernel waits (bounded) for its own copies, frees its
+ * tensor memory, returns, and the solve reports AFI_ETIMEOUT instead of
+ * hanging the GPU.  This entry point runs that path
  * on purpose: one CTA allocates tensor memory, waits at most `polls` polls
  * (1 <= polls <= 2^22) on an mbarrier that nothing ever arrives on, frees
  * the tensor memory and returns.  Returns AFI_ETIMEOUT when the wait ran out
