@@ -151,6 +151,14 @@ class AFIETI:
             self.A = sp.block_diag(blocks, format="csr")
         return self.A
 
+    def mass(self, k):
+        """The scalar mapped mass M^(k) (dense), computed once per patch."""
+        if not hasattr(self, "_mass"):
+            self._mass = {}
+        if k not in self._mass:
+            self._mass[k], _ = assembly.mass_block(self.geo[k])
+        return self._mass[k]
+
     def load(self, coeffs):
         """f^(k) = M^(k) c^(k) stacked over patches."""
         return np.concatenate([assembly.load_from_coeffs(g, coeffs[k])
@@ -235,7 +243,7 @@ class AFIETI:
         for k, g in enumerate(self.geo):
             sl = slice(self.off[k], self.off[k + 1])
             Ak = A[sl][:, sl].tocsc()
-            Mk, _ = assembly.mass_block(g)
+            Mk = self.mass(k)
             Md = sp.block_diag([sp.csr_matrix(Mk)] * self.dim)
             PA = spla.splu((Ak + Md / self.H[k] ** 2).tocsc())
             mask = np.tile(fd.interior_mask(g.ns), self.dim)
@@ -282,9 +290,8 @@ class AFIETI:
         out = []
         for k, g in enumerate(self.geo):
             sl = slice(self.off[k], self.off[k + 1])
-            Mk, _ = assembly.mass_block(g)
             lam, mu = self.prob.lame[k]
-            out.append(geo.GeoLocal(g, lam, mu, self.H[k], A[sl][:, sl].tocsr(), Mk))
+            out.append(geo.GeoLocal(g, lam, mu, self.H[k], A[sl][:, sl].tocsr(), self.mass(k)))
         self._geol = out
         return out
 
