@@ -240,24 +240,30 @@ afi_status afi_apply(afi_ctx *ctx, afi_operator op, const double *x_dev, double 
  * precision copies of the eigenvectors are built at setup). */
 afi_status afi_set_precision(afi_ctx *ctx, afi_fd_precision prec);
 
-/* Allocation-free fast diagonalization (the paper has no counterpart: this
- * serves callers that may not allocate device memory where they need a local
- * solve, e.g. code being recorded into a CUDA graph that must contain no
- * allocation, real-time loops on a fixed memory budget, or plug-ins whose
- * host framework owns all device memory).  Computes, for nblk FP64 tensors
- * of one shape stacked in r and s ([nblk][n3][n2][n1], i1 fastest, device),
+/* Allocation-free fast diagonalization.  The paper has no counterpart: this
+ * entry point serves callers that may not allocate device memory where they
+ * need a local solve, e.g. code being recorded into a CUDA graph that must
+ * contain no allocation, real-time loops on a fixed memory budget, or
+ * plug-ins whose host framework owns all device memory.  For nblk FP64
+ * tensors of one shape stacked in r and s ([nblk][n3][n2][n1], i1 fastest,
+ * device memory) it computes
  *     s = (U3 x U2 x U1) Lambda^{-1} (U3 x U2 x U1)^T r,
  *     Lambda[i1,i2,i3] = scale * (coef[0] D1[i1] + coef[1] D2[i2]
  *                                 + coef[2] D3[i3] + shift),
- * i.e. Algorithm 1 with caller-provided eigen data: U_l is n_l x n_l
- * row-major (row = basis index, column = mode), D_l has n_l entries, all in
- * device memory; coef is a host array.  For 2D data pass n3 = 1 and
- * U3 = D3 = NULL.  Example: coef = (c_1, c_2, c_3), shift = 1,
- * scale = H^{d-2} gives P_A^{inex,-1} of eq. (5.9); shift = 0, scale = 1 and
- * interior eigen data give eq. (5.10).
+ * where U_l is n_l x n_l row-major (row = basis index, column = mode) and
+ * D_l has n_l entries, all in device memory; coef is a host array of three.
+ * With U_l, D_l the generalised eigenvectors (U^T M U = I) and eigenvalues
+ * of a pair of univariate matrices (K_l, M_l), s solves the Kronecker-sum
+ * system whose matrix is scale * (sum_l coef[l] K_l (x) the M's of the other
+ * directions + shift * M_3 x M_2 x M_1).
+ * Three directions are used exactly when U3 and D3 are both given (n3 may
+ * then be 1); pass U3 = D3 = NULL with n3 = 1 for two directions (coef[2]
+ * is then ignored).  One of U3, D3 alone, or n3 > 1 without them, returns
+ * AFI_EINVAL.
  * Scratch: a file-scope device array of 2^21 doubles (16 MiB) that every GPU
  * loading the library holds until the process exits; 2 * nblk * n1*n2*n3
- * must not exceed 2^21, larger requests return AFI_EINVAL without running.
+ * must not exceed 2^21 (checked without overflow), larger requests return
+ * AFI_EINVAL without running.
  * The first call on a device looks up the array's address (with that device
  * current); make that first call before any stream capture.  All calls share
  * the array, so calls whose executions overlap on the GPU (different streams

@@ -48,7 +48,8 @@ __global__ void __launch_bounds__(256) k_fd_static(int n1, int n2, int n3, const
                                                    const double *D1, const double *D2,
                                                    const double *D3, double c1, double c2,
                                                    double c3, double shift, double scale,
-                                                   const double *r, double *s, double *scratch) {
+                                                   int nd, const double *r, double *s,
+                                                   double *scratch) {
   const int N = n1 * n2 * n3;
   const long long blk = blockIdx.x;
   double *cur = scratch + 2 * blk * N, *oth = cur + N;
@@ -58,7 +59,6 @@ __global__ void __launch_bounds__(256) k_fd_static(int n1, int n2, int n3, const
   __syncthreads();
   const double *U[3] = {U1, U2, U3};
   const int n[3] = {n1, n2, n3};
-  const int nd = (n3 > 1) ? 3 : 2;
   for (int d = 0; d < nd; ++d) {
     fds_mode(cur, oth, U[d], n[d], d, n1, n2, n3, true);
     __syncthreads();
@@ -109,22 +109,31 @@ extern "C" afi_status afi_fd_apply_static(int n1, int n2, int n3, const double *
                                           const double *D2, const double *D3, const double coef[3],
                                           double shift, double scale, const double *r, double *s,
                                           int nblk, void *stream) {
+  // three directions exactly when the third direction's eigen data is given
+  const bool has3 = (U3 != nullptr) || (D3 != nullptr);
   if (n1 < 1 || n2 < 1 || n3 < 1 || nblk < 1 || !coef || !r || !s || !U1 || !U2 || !D1 || !D2 ||
-      (n3 > 1 && (!U3 || !D3))) {
-    set_error("afi_fd_apply_static: invalid argument");
+      (has3 && (!U3 || !D3)) || (!has3 && n3 != 1)) {
+    set_error("afi_fd_apply_static: invalid argument (3D data needs both U3 and D3; "
+              "2D data needs n3 == 1)");
     return AFI_EINVAL;
   }
-  const long long need = 2LL * nblk * (long long)n1 * n2 * n3;
-  if (need > kFdStaticMaxDoubles) {
-    set_error("afi_fd_apply_static: 2 * nblk * n1 * n2 * n3 = " + std::to_string(need) +
-              " doubles exceeds the static scratch of " + std::to_string(kFdStaticMaxDoubles));
-    return AFI_EINVAL;
+  // 2 * nblk * n1 * n2 * n3 <= kFdStaticMaxDoubles, checked factor by factor
+  // so that no product can overflow
+  long long room = kFdStaticMaxDoubles / 2;
+  const long long f[4] = {n1, n2, n3, nblk};
+  for (long long x : f) {
+    if (x > room) {
+      set_error("afi_fd_apply_static: 2 * nblk * n1 * n2 * n3 exceeds the static scratch of " +
+                std::to_string(kFdStaticMaxDoubles) + " doubles");
+      return AFI_EINVAL;
+    }
+    room /= x;
   }
   double *scratch = nullptr;
   AFI_TRY(static_scratch(&scratch));
   launch(k_fd_static, nblk, 256, 0, reinterpret_cast<cudaStream_t>(stream), n1, n2, n3, U1, U2,
-         n3 > 1 ? U3 : U1, D1, D2, n3 > 1 ? D3 : D1, coef[0], coef[1], coef[2], shift, scale, r, s,
-         scratch);
+         has3 ? U3 : U1, D1, D2, has3 ? D3 : D1, coef[0], coef[1], coef[2], shift, scale,
+         has3 ? 3 : 2, r, s, scratch);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }

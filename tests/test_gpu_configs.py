@@ -2,7 +2,7 @@
 
 C3: quarter annulus, 6x4x3 patches with per-column element counts and p = 4
 (uneven tensors, some too large for the single-CTA tensor-core FD, which then
-runs on the FP32 SIMT kernel): full TF32 solve to 1e-8 with sampled oracle
+run on the three-pass tensor-core kernels): full TF32 solve to 1e-8 with sampled oracle
 stiffness rows and equilibrium rows, vanishing jumps, sampled FD blocks.
 C5: twisted box, 8x8x4 patches, p = 4, 48^3 elements (108 M DoF per
 right-hand side; its stencil would need 1.9 TB): a local-solvers-only

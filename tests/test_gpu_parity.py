@@ -2,16 +2,30 @@
 C ABI, on seeded inputs spanning several tiles and ragged sizes (2D and 3D,
 degrees 2-4, identity, jittered, annulus and twisted geometries).
 
+Every comparison is made block by block (tests/blocks.py): the largest
+relative error over the (patch, component) tensors of a torn vector and over
+the (component, patch) runs of a multiplier vector, so that one wrong block
+cannot hide among many right ones.
+
 Tolerances (FP64 paths): operators that are sums of O(10^3) products are
-compared at 1e-11 relative to the norm of the result; solves at 1e-7
+compared at 1e-11 relative to the norm of the block; solves at 1e-7
 relative (tolerance 1e-10 of the iterative solve against the direct solve).
-FP32 local solvers: 2e-5 relative per application (FP32 unit roundoff times
-the O(n) accumulation length and the conditioning of U); TF32 (operands
-truncated to a 10-bit mantissa, error up to 9.8e-4 each) 1e-2 and BF16 (7-bit
-mantissa, 3.9e-3) 3e-2 per application, the same accumulation argument over
-six mode products.  Whatever the local-solver
-precision, the converged solution is compared at 1e-7 (the preconditioner
-changes only the iteration)."""
+Local solvers in reduced precision, per application: FP32 2e-5 (FP32 unit
+roundoff times the O(n) accumulation length and the conditioning of U);
+TF32 (operands truncated to a 10-bit mantissa, error up to 9.8e-4 each)
+1e-2 and BF16 (7-bit mantissa, 3.9e-3) 3e-2, the same accumulation argument
+over six mode products.  Operators built on a local solve inherit that
+tolerance times the cancellation that follows it, which the oracle measures
+on the same input: for the Schur block, S theta = A_GG theta + A_GI v_I with
+v_I the interior solve, a relative error e in v_I gives an error of about
+e ||A_GI v_I|| / ||S theta|| in the block; for the preconditioner,
+P_u P_A^{-1} P_u and P_chi P_S P_chi, the ratio of the unprojected to the
+projected result.  Beside these oracle checks every composite operator is
+checked against the composition of the GPU's own parts in FP64 (tight), so
+a wiring error cannot hide under a loose tolerance.  Whatever the
+local-solver precision, the converged solution is compared at 1e-7 (the
+preconditioner changes only the iteration), and the TF32/BF16 iteration
+counts stay within 10% (plus 2) of the oracle's FP64 count."""
 import numpy as np
 import pytest
 
@@ -19,16 +33,17 @@ import afi_workloads as W
 from oracle import fd as ofd
 from oracle.ieti import AFIETI
 
+from blocks import block_rel, interior_blocks, mult_blocks, saddle_blocks, torn_blocks
+
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 CASES = ["C1-small", "C1", "C2-small", "C4-small", "C5-small"]
+PREC_TOL = {"fp64": 1e-10, "fp32": 2e-5, "tf32": 1e-2, "bf16": 3e-2}
 
 
-def rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+def T(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
 
 
 @pytest.fixture(scope="module", params=CASES)
@@ -44,8 +59,41 @@ def case(request):
     s.close()
 
 
-def T(x):
-    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+def block_errs(a, ref, blocks):
+    """Per-block relative errors (inf where a zero reference block is not
+    reproduced exactly)."""
+    out = []
+    for lo, hi in blocks:
+        rn = np.linalg.norm(ref[lo:hi])
+        dn = np.linalg.norm(a[lo:hi] - ref[lo:hi])
+        out.append(dn / rn if rn > 0 else (0.0 if dn == 0 else np.inf))
+    return np.array(out)
+
+
+def schur_parts(orc, t):
+    """Oracle S_hat_H t and, per torn block, the part H^{d-2} (A_hat [0; v_I])_G
+    that the interior solve v_I contributes (the term a local-solver error
+    enters through)."""
+    S = orc.S_hat_H(t)
+    C = np.zeros_like(t)
+    for k, (per, mask, Hs) in enumerate(orc._local()):
+        for l in range(orc.dim):
+            a = orc.dof(k, l, 0)
+            sl = slice(a, a + orc.N[k])
+            Ah, AII = per[l][1], per[l][2]
+            v = np.where(mask, 0.0, t[sl])
+            vI = -AII.solve((Ah @ v)[mask])
+            w = np.zeros(orc.N[k])
+            w[mask] = vI
+            C[sl] = np.where(mask, 0.0, Hs * (Ah @ w))
+    return S, C
+
+
+def amp(num, den, blocks, num_blocks=None):
+    """Per block ||num||_(num block) / ||den||_block, at least 1."""
+    nb = num_blocks or blocks
+    return np.array([max(1.0, np.linalg.norm(num[a:b]) / max(np.linalg.norm(den[c:d]), 1e-300))
+                     for (a, b), (c, d) in zip(nb, blocks)])
 
 
 def test_sizes(case):
@@ -57,7 +105,7 @@ def test_load_vector(case):
     _, prob, orc, s = case
     c = W.body_force_coeffs(prob)
     f = s.load_vector(c).cpu().numpy()
-    assert rel(f, orc.load(c)) < 1e-13
+    assert block_rel(f, orc.load(c), torn_blocks(orc)) < 1e-13
 
 
 def test_stiffness_matvec(case):
@@ -65,7 +113,7 @@ def test_stiffness_matvec(case):
     from paper_2001_09626_gb300 import afieti as A
     x = W.torn_random(prob, 11)[0]
     y = s.apply(A.AFI_OP_STIFFNESS, T(x)).cpu().numpy()
-    assert rel(y, orc.A @ x) < 1e-11
+    assert block_rel(y, orc.A @ x, torn_blocks(orc)) < 1e-11
 
 
 def test_jumps_and_projections(case):
@@ -76,27 +124,26 @@ def test_jumps_and_projections(case):
     np.testing.assert_array_equal(s.apply(A.AFI_OP_B, T(x)).cpu().numpy(), orc.B @ x)
     np.testing.assert_allclose(s.apply(A.AFI_OP_BT, T(lam)).cpu().numpy(), orc.B.T @ lam,
                                rtol=0, atol=1e-15)
-    assert rel(s.apply(A.AFI_OP_PCHI, T(lam)).cpu().numpy(), orc.P_chi(lam)) < 1e-10
-    assert rel(s.apply(A.AFI_OP_PU, T(x)).cpu().numpy(), orc.P_u(x)) < 1e-11
+    assert block_rel(s.apply(A.AFI_OP_PCHI, T(lam)).cpu().numpy(), orc.P_chi(lam),
+                     mult_blocks(orc)) < 1e-10
+    assert block_rel(s.apply(A.AFI_OP_PU, T(x)).cpu().numpy(), orc.P_u(x), torn_blocks(orc)) < 1e-11
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5), ("tf32", 1e-2),
-                                      ("bf16", 3e-2)])
-def test_fd_apply(case, prec, tol):
+@pytest.mark.parametrize("prec", list(PREC_TOL))
+def test_fd_apply(case, prec):
     _, prob, orc, s = case
     from paper_2001_09626_gb300 import afieti as A
     s.set_precision(prec)
     try:
         x = W.torn_random(prob, 13)[0]
         y = s.apply(A.AFI_OP_PA_INV, T(x)).cpu().numpy()
-        assert rel(y, orc.PA_inv(x)) < tol
+        assert block_rel(y, orc.PA_inv(x), torn_blocks(orc)) < PREC_TOL[prec]
     finally:
         s.set_precision("fp64")
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5), ("tf32", 1e-2),
-                                      ("bf16", 3e-2)])
-def test_interior_fd(case, prec, tol):
+@pytest.mark.parametrize("prec", list(PREC_TOL))
+def test_interior_fd(case, prec):
     _, prob, orc, s = case
     s.set_precision(prec)
     try:
@@ -110,40 +157,97 @@ def test_interior_fd(case, prec, tol):
                 refs.append(per[l][2].solve(r))
         r = np.concatenate(blocks)
         out = s.fd(T(r), interior=True).cpu().numpy()
-        assert rel(out, np.concatenate(refs)) < tol
+        assert block_rel(out, np.concatenate(refs), interior_blocks(orc)) < PREC_TOL[prec]
     finally:
         s.set_precision("fp64")
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
-def test_schur_and_PS(case, prec, tol):
+@pytest.mark.parametrize("prec", list(PREC_TOL))
+def test_schur_and_PS(case, prec):
+    """Schur block and P_S against the oracle, per block, at the local
+    solver's tolerance times the cancellation the oracle measures; and P_S
+    against the oracle's glue (B B^T)^{-1} B [.] B^T (B B^T)^{-1} around the
+    GPU's own Schur block (FP64 glue, tight)."""
     _, prob, orc, s = case
     from paper_2001_09626_gb300 import afieti as A
+    tol = PREC_TOL[prec]
+    tb, mb = torn_blocks(orc), mult_blocks(orc)
     s.set_precision(prec)
     try:
         t = W.torn_random(prob, 15)[0] * orc.shell
         y = s.apply(A.AFI_OP_SCHUR, T(t)).cpu().numpy()
-        assert rel(y, orc.S_hat_H(t)) < tol
+        S, C = schur_parts(orc, t)
+        e = block_errs(y, S, tb)
+        k = amp(C, S, tb)
+        assert np.all(e <= tol * k), (float(e.max()), float((e / k).max()))
         lam = np.random.default_rng(4).uniform(-1, 1, orc.nc)
-        assert rel(s.apply(A.AFI_OP_PS, T(lam)).cpu().numpy(), orc.P_S(lam)) < tol
+        ps = s.apply(A.AFI_OP_PS, T(lam)).cpu().numpy()
+        tl = orc.B.T @ orc.BBt_lu.solve(lam)
+        S2, C2 = schur_parts(orc, tl)
+        ref = orc.BBt_lu.solve(orc.B @ S2)
+        cref = orc.BBt_lu.solve(orc.B @ np.abs(C2))
+        e = block_errs(ps, ref, mb)
+        k = amp(cref, ref, mb)
+        assert np.all(e <= tol * k), (float(e.max()), float((e / k).max()))
+        # composition with the GPU's own Schur block, exact up to FP64 glue
+        sg = s.apply(A.AFI_OP_SCHUR, T(tl)).cpu().numpy()
+        comp = orc.BBt_lu.solve(orc.B @ sg)
+        assert block_rel(ps, comp, mb) < 1e-9
     finally:
         s.set_precision("fp64")
 
 
-def test_precond_and_saddle(case):
+@pytest.mark.parametrize("prec", list(PREC_TOL))
+def test_precond_and_saddle(case, prec):
+    """B^{-1} of eq. 4.9 at every local-solver precision: per block against
+    the oracle (tolerance times the projection's cancellation) and against
+    P_u P_A^{-1} P_u and P_chi P_S P_chi composed from the GPU's own local
+    solvers with the oracle's FP64 projections (tight).  The saddle operator
+    is FP64 and independent of the local solvers."""
     _, prob, orc, s = case
     from paper_2001_09626_gb300 import afieti as A
     rng = np.random.default_rng(16)
     x = rng.uniform(-1, 1, orc.ndof + orc.nc)
-    y = s.apply(A.AFI_OP_SADDLE, T(x)).cpu().numpy()
-    ref = np.concatenate(orc.op(x[:orc.ndof], x[orc.ndof:]))
-    assert rel(y, ref) < 1e-11
-    z = s.apply(A.AFI_OP_PRECOND, T(x)).cpu().numpy()
-    refz = np.concatenate(orc.precond_apply(x[:orc.ndof], x[orc.ndof:]))
-    assert rel(z, refz) < 1e-10
+    n = orc.ndof
+    sb = saddle_blocks(orc)
+    if prec == "fp64":
+        y = s.apply(A.AFI_OP_SADDLE, T(x)).cpu().numpy()
+        assert block_rel(y, np.concatenate(orc.op(x[:n], x[n:])), sb) < 1e-11
+    tol = PREC_TOL[prec]
+    s.set_precision(prec)
+    try:
+        z = s.apply(A.AFI_OP_PRECOND, T(x)).cpu().numpy()
+        refw, refc = orc.precond_apply(x[:n], x[n:])
+        ref = np.concatenate([refw, refc])
+        if prec == "fp64":
+            assert block_rel(z, ref, sb) < 1e-10
+        else:
+            # primal: the FD error of patch k, projected by P_u of patch k
+            fw = orc.PA_inv(orc.P_u(x[:n]))
+            tb = torn_blocks(orc)
+            pb = [(int(orc.off[k]), int(orc.off[k + 1])) for k in range(orc.np)
+                  for _ in range(orc.dim)]
+            e = block_errs(z[:n], refw, tb)
+            k = amp(fw, refw, tb, pb)
+            assert np.all(e <= tol * k), (float(e.max()), float((e / k).max()))
+            # multiplier: the P_S error, projected by the global P_chi
+            pc = orc.P_chi(x[n:])
+            psr = orc.P_S(pc)
+            mb = mult_blocks(orc)
+            whole = [(0, orc.nc)] * len(mb)
+            e = block_errs(z[n:], refc, mb)
+            k = amp(psr, refc, mb, whole)
+            assert np.all(e <= 10 * tol * k), (float(e.max()), float((e / k).max()))
+        # composition with the GPU's own P_A^{-1} and P_S
+        fdg = s.apply(A.AFI_OP_PA_INV, T(orc.P_u(x[:n]))).cpu().numpy()
+        psg = s.apply(A.AFI_OP_PS, T(orc.P_chi(x[n:]))).cpu().numpy()
+        comp = np.concatenate([orc.P_u(fdg), orc.P_chi(psg)])
+        assert block_rel(z, comp, sb) < 1e-9
+    finally:
+        s.set_precision("fp64")
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", list(PREC_TOL))
 def test_solve_matches_direct(case, prec):
     name, prob, orc, s = case
     s.set_precision(prec)
@@ -154,15 +258,20 @@ def test_solve_matches_direct(case, prec):
         info = s.last_info
         ud, ld = orc.direct_solve(f)
         assert info["relres_true"] <= 1e-10
-        assert rel(u.cpu().numpy(), ud) < 1e-7
-        assert rel(lam.cpu().numpy(), ld) < 1e-7
+        assert block_rel(u.cpu().numpy(), ud, torn_blocks(orc)) < 1e-7
+        assert block_rel(lam.cpu().numpy(), ld, mult_blocks(orc)) < 1e-7
         assert np.linalg.norm(orc.B @ u.cpu().numpy()) < 1e-8 * np.linalg.norm(ud)
+        if not hasattr(orc, "_test_iters"):
+            orc._test_iters = orc.solve(f, tol=1e-10)[2]["iters"]
+        oit = orc._test_iters
         if prec == "fp64":
             # same iterates; the stopping iteration follows the true-residual
             # check schedule, which rounding can move by a few iterations
-            _, _, oinfo = orc.solve(f, tol=1e-10)
-            assert abs(info["iters"] - oinfo["iters"]) <= max(2, 0.05 * oinfo["iters"]), \
-                (info["iters"], oinfo["iters"])
+            assert abs(info["iters"] - oit) <= max(2, 0.05 * oit), (info["iters"], oit)
+        else:
+            # an inexact preconditioner in reduced precision may cost a few
+            # iterations, not more
+            assert info["iters"] <= 1.1 * oit + 2, (info["iters"], oit)
     finally:
         s.set_precision("fp64")
 
@@ -175,10 +284,10 @@ def test_adjoint_gradients(case):
     g = s.lame_grad(u, u).cpu().numpy()
     ud, _ = orc.direct_solve(f)
     ref = adjoint.lame_gradient(orc, ud, ud)
-    assert rel(g, ref) < 1e-7
+    assert np.all(np.abs(g - ref) <= 1e-7 * np.abs(ref) + 1e-9 * np.abs(ref).max()), (g, ref)
     # adjoint state for J = f^T u equals u
     z2, _ = s.solve_adjoint(T(f))
-    assert rel(z2.cpu().numpy(), ud) < 1e-7
+    assert block_rel(z2.cpu().numpy(), ud, torn_blocks(orc)) < 1e-7
 
 
 def test_invalid_arguments(case):
