@@ -129,6 +129,36 @@ typedef struct {
                                       and AFI_OP_SCHUR then apply these;
                                       fd_apply stays the FD of Algorithm 1,
                                       and afi_options.prec has no effect */
+#define AFI_VARIANT_GEO 32         /* geometry-inclusion inexact local solvers
+                                      (Section 5.2.3), the variant of the
+                                      paper's experiments: per (patch,
+                                      component l) the diagonal of the
+                                      elasticity coefficient C_l and |det J|
+                                      are fitted at the Gauss points by
+                                      products of univariate factors (in the
+                                      logarithm, by Diliberto-Straus
+                                      mid-range sweeps until no factor moves
+                                      by more than 1e-14, at most 500), which
+                                      give the univariate K~_{l,m}, M~_{l,m}
+                                      of eq. 5.11; then
+                                      P_A^{-1} = D_A^{-1/2} (A~_l +
+                                      H^{-2} M~_l)^{-1} D_A^{-1/2} (eq. 5.12)
+                                      by Algorithm 1 on the eigenpairs of
+                                      (K~_{l,m}, M~_{l,m}), and the Schur
+                                      block is D_S^{1/2} S~_l D_S^{1/2} with
+                                      S~_l the Schur complement of A~_l
+                                      (eq. 5.13), D_A and D_S the diagonal
+                                      scalings that restore the diagonals of
+                                      A_ll + H^{-2} M and A_ll.  Applies to
+                                      fd_apply (interior = 0 and 1),
+                                      AFI_OP_PA_INV, AFI_OP_SCHUR, AFI_OP_PS,
+                                      AFI_OP_PRECOND and the solves, at every
+                                      afi_options.prec.  Needs the geometry:
+                                      with AFI_VARIANT_LOCAL_ONLY or
+                                      AFI_VARIANT_EXACT it returns
+                                      AFI_EINVAL.  The fit and the per-(patch,
+                                      component) tables count as local-solver
+                                      setup (afi_info.t_fd_setup_ms). */
 
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
  * preconditioned residual estimate and then the true FP64 residual

@@ -168,6 +168,7 @@ AFI_VARIANT_FD_SLAB = 2
 AFI_VARIANT_STENCIL_F64 = 4
 AFI_VARIANT_FORCE_RESTART = 8
 AFI_VARIANT_EXACT = 16
+AFI_VARIANT_GEO = 32
 
 
 def af_ieti_setup(prob, prec="fp64", tol=1e-8, maxit=2000, use_graph=False, variant=0):

@@ -100,6 +100,9 @@ struct Tab1D {
   long long tcB[2][2][2];      // tensor-core B operands, byte offsets in tcpool:
                                // [bf16][interior][back]; forward B[a][k] = U[k][a],
                                // back B[i][k] = U[i][k], canonical K-major layout
+  long long wK, wM;            // geometry-inclusion tables: per-quadrature-point factors
+                               // nu (in K) and beta (in M) of eq. 5.11; -1 for the
+                               // plain univariate K_hat, M_hat
 };
 
 // Per-patch descriptor (device-side POD).
@@ -121,6 +124,18 @@ struct DevPatch {
   long long xoff;   // control point offset (doubles)
   double lam, mu, Hs;  // Lame values, H^{d-2}
   double H;            // patch diameter H^(k)
+  // Local solvers of component l (FD of P_A and of the interior block, the
+  // Schur block): univariate table per direction m, the coefficient of the
+  // stiffness term in direction m, the mass shift and the overall scale:
+  //   Lambda_l = lscale (sum_m lcf[l][m] D_m + lshift),  S scaled by lscale.
+  // Plain parametric solvers (eqs. 5.6, 5.7): ltab[l][m] = tab[m],
+  // lcf = 2 mu + lambda on m = l and mu elsewhere, lshift = 1, lscale =
+  // H^{d-2}.  Geometry inclusion (eqs. 5.12, 5.13): tables of the fitted
+  // K~_{l,m}, M~_{l,m}, lcf = 1, lshift = H^{-2}, lscale = 1.
+  int ltab[3][3];
+  double lcf[3][3];
+  double lshift, lscale;
+  long long qloff;     // geometry-inclusion fit: first per-direction Gauss-point slot
 };
 
 // Split of the patches between the tensor-core FD (tensors that fit one CTA)
@@ -177,6 +192,12 @@ struct afi_ctx {
   long long *ex_koff = nullptr, *ex_aoff = nullptr;  // their per-patch offsets
   bool mv_exact = false;                      // apply the FP64 stencil even if pairs exist
   double *qgeo = nullptr; long long nqp = 0;  // [DIM*DIM + 1][nqp] SoA
+  // geometry-inclusion local solvers (AFI_VARIANT_GEO, Section 5.2.3)
+  bool geo = false;
+  int nbase_tab = 0;                          // tables before the per-(patch, component) ones
+  double *geo_dA = nullptr;                   // D_A^{-1/2} per dof (eq. 5.12)
+  double *geo_dS = nullptr;                   // D_S^{1/2} per dof (eq. 5.13)
+  double *geo_tmp = nullptr;                  // n_dof scratch of the scaled FD
 
   // constraints
   int2 *row_copy = nullptr;      // (dofA, dofB or -1) per row
@@ -286,6 +307,10 @@ afi_status fd_tc_ready(afi_ctx *c);
 // precision uses the shared local-solver scratch slab
 bool fd_uses_scratch(afi_ctx *c, int interior);
 afi_status fd_tc_tables(afi_ctx *c);
+// geo.cu (geometry-inclusion local solvers, Section 5.2.3)
+afi_status geo_setup(afi_ctx *c);
+afi_status geo_scale(afi_ctx *c, const double *x, const double *d, double *y, long n, int nrhs,
+                     cudaStream_t st);
 // fd_slab.cu (three-pass tensor-core FD for tensors larger than one CTA)
 afi_status slab_prepare(afi_ctx *c, int *dyn_max);
 afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> &cand,

@@ -113,7 +113,7 @@ __device__ T *fd_tensor(T *cur, T *oth, const DevPatch &pt, const Tab1D *tabs, c
   const T *Uf[3], *Ub[3], *Dv[3];
   int ld[3];
   for (int d = 0; d < 3; ++d) {
-    const Tab1D tb = tabs[pt.tab[d]];
+    const Tab1D tb = tabs[pt.ltab[l][d]];
     Uf[d] = tpool + (interior ? tb.Uip : tb.Up);
     Ub[d] = tpool + (interior ? tb.Uipt : tb.Upt);
     Dv[d] = tpool + (interior ? tb.Di : tb.D);
@@ -124,12 +124,12 @@ __device__ T *fd_tensor(T *cur, T *oth, const DevPatch &pt, const Tab1D *tabs, c
     __syncthreads();
     T *t = cur; cur = oth; oth = t;
   }
-  const T cl = (T)(2.0 * pt.mu + pt.lam), mu = (T)pt.mu, hs = (T)pt.Hs;
-  const T c0 = (l == 0) ? cl : mu, c1 = (l == 1) ? cl : mu, c2 = (l == 2) ? cl : mu;
+  const T hs = (T)pt.lscale, sh = (T)pt.lshift;
+  const T c0 = (T)pt.lcf[l][0], c1 = (T)pt.lcf[l][1], c2 = (T)pt.lcf[l][2];
   for (int idx = threadIdx.x; idx < D.N; idx += blockDim.x) {   // q~ = Lambda^{-1} r~
     const int i1 = idx % D.n[0], i2 = (idx / D.n[0]) % D.n[1], i3 = idx / (D.n[0] * D.n[1]);
     T lam = c0 * Dv[0][i1] + c1 * Dv[1][i2] + (dim == 3 ? c2 * Dv[2][i3] : T(0));
-    if (!interior) lam = hs * (lam + T(1));
+    if (!interior) lam = hs * (lam + sh);
     cur[idx] = cur[idx] / lam;
   }
   __syncthreads();
@@ -200,18 +200,34 @@ static afi_status fd_launch(afi_ctx *c, int interior, const double *r, double *s
   return AFI_OK;
 }
 
-afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st,
-                  int nrhs) {
+static afi_status fd_dispatch(afi_ctx *c, int interior, const double *r, double *s,
+                              cudaStream_t st, int nrhs) {
   switch (c->opt.prec) {
     case AFI_FD_FP64: return fd_launch<double>(c, interior, r, s, st, nrhs);
     case AFI_FD_FP32: return fd_launch<float>(c, interior, r, s, st, nrhs);
     case AFI_FD_TF32:
     case AFI_FD_BF16:
-      // tensor cores for the patches whose tensors fit one CTA, FP32 SIMT
-      // for the others
+      // tensor cores: the single-CTA kernel for the tensors that fit one
+      // CTA, the three-pass kernels for larger ones, and FP32 SIMT only for
+      // tensors that neither takes
       return fd_tc_run(c, interior, r, s, st, nrhs);
     default: set_error("local-solver precision not available"); return AFI_EINVAL;
   }
+}
+
+afi_status fd_run(afi_ctx *c, int interior, const double *r, double *s, cudaStream_t st,
+                  int nrhs) {
+  if (c->geo && !interior) {
+    // geometry inclusion (eq. 5.12): D_A^{-1/2} (A~_l + H^{-2} M~_l)^{-1} D_A^{-1/2}
+    const long n = c->n_dof;
+    for (int j = 0; j < nrhs; ++j) {
+      AFI_TRY(geo_scale(c, r + (long long)j * n, c->geo_dA, c->geo_tmp, n, 1, st));
+      AFI_TRY(fd_dispatch(c, 0, c->geo_tmp, s + (long long)j * n, st, 1));
+      AFI_TRY(geo_scale(c, s + (long long)j * n, c->geo_dA, s + (long long)j * n, n, 1, st));
+    }
+    return AFI_OK;
+  }
+  return fd_dispatch(c, interior, r, s, st, nrhs);
 }
 
 afi_status fd_simt_list(afi_ctx *c, int interior, const int *list, int count, int maxN,

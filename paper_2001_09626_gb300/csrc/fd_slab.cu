@@ -144,13 +144,13 @@ __global__ void __launch_bounds__(256, 4) k_fd_plane(const DevPatch *P, const Ta
   }
   __syncthreads();
   // both products use one B slot when directions 1 and 2 share a table
-  const int slot1 = (pt.tab[0] == pt.tab[1]) ? 0 : 1;
+  const int slot1 = (pt.ltab[l][0] == pt.ltab[l][1]) ? 0 : 1;
   if (tid == 0) {
     const uint32_t b0 = (uint32_t)(rup(n1, 16) * rup(n1, KSTEP) * (int)sizeof(T));
     const uint32_t b1 = (uint32_t)(rup(n2, 16) * rup(n2, KSTEP) * (int)sizeof(T));
     expect_tx(&tma_bar, slot1 ? b0 + b1 : b0);
-    bulk_g2s(bm, tcpool + tabs[pt.tab[0]].tcB[FMT == 1][interior][BACK], b0, &tma_bar);
-    if (slot1) bulk_g2s(bm + bsz, tcpool + tabs[pt.tab[1]].tcB[FMT == 1][interior][BACK], b1, &tma_bar);
+    bulk_g2s(bm, tcpool + tabs[pt.ltab[l][0]].tcB[FMT == 1][interior][BACK], b0, &tma_bar);
+    if (slot1) bulk_g2s(bm + bsz, tcpool + tabs[pt.ltab[l][1]].tcB[FMT == 1][interior][BACK], b1, &tma_bar);
   }
   {
     uint4 *zp = reinterpret_cast<uint4 *>(A);
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
   __syncthreads();
   const uint32_t bbytes = (uint32_t)(rup(n3, 16) * rup(n3, KSTEP) * (int)sizeof(T));
   if (tid == 0) {
-    const Tab1D &tb = tabs[pt.tab[2]];
+    const Tab1D &tb = tabs[pt.ltab[l][2]];
     stage_b(&tma_bar, bm, bsz, tcpool, tb.tcB[FMT == 1][interior][0], bbytes,
             tb.tcB[FMT == 1][interior][1], bbytes);
   }
@@ -429,11 +429,11 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
   const int q = warp & 3, half = warp >> 2;
   const int row = q * 32 + lane;
   // Lambda = c1 D1[a1] + c2 D2[a2] + c3 D3[a3] (+1, times H^{d-2}, for P_A)
-  const float cl = (float)(2.0 * pt.mu + pt.lam), mu = (float)pt.mu, hs = (float)pt.Hs;
-  const float c0 = (l == 0) ? cl : mu, c1 = (l == 1) ? cl : mu, c2 = (l == 2) ? cl : mu;
-  const float *D0 = fpool + (interior ? tabs[pt.tab[0]].Di : tabs[pt.tab[0]].D);
-  const float *D1 = fpool + (interior ? tabs[pt.tab[1]].Di : tabs[pt.tab[1]].D);
-  const float *D2 = fpool + (interior ? tabs[pt.tab[2]].Di : tabs[pt.tab[2]].D);
+  const float hs = (float)pt.lscale, shf = (float)pt.lshift;
+  const float c0 = (float)pt.lcf[l][0], c1 = (float)pt.lcf[l][1], c2 = (float)pt.lcf[l][2];
+  const float *D0 = fpool + (interior ? tabs[pt.ltab[l][0]].Di : tabs[pt.ltab[l][0]].D);
+  const float *D1 = fpool + (interior ? tabs[pt.ltab[l][1]].Di : tabs[pt.ltab[l][1]].D);
+  const float *D2 = fpool + (interior ? tabs[pt.ltab[l][2]].Di : tabs[pt.ltab[l][2]].D);
   float lab = 0.f;
   if (row < nl) {
     const int line = line0 + row, a2 = line / n1, a1 = line - a2 * n1;
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
           for (int jj = 0; jj < 8; ++jj) {
             const int j = j0 + jj;
             float lam = lab + c2 * (j < n3 ? D2[j] : 0.f);
-            if (!interior) lam = hs * (lam + 1.f);
+            if (!interior) lam = hs * (lam + shf);
             x[jj] = (j < n3) ? __fdividef(__uint_as_float(raw[u][jj]), lam) : 0.f;
           }
           if (j0 < Kp) {
@@ -575,7 +575,8 @@ afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> 
     const int ntp = std::max(tcols_p, s.tcols_p);
     const int ncl = std::max(cap_l, s.cap_l), nbl = std::max(bsz_l, s.bsz_l);
     const int ntl = std::max(tcols_l, s.tcols_l);
-    const int nsp = std::max(nslot_p, p.tab[0] == p.tab[1] ? 1 : 2);
+    int nsp = nslot_p;
+    for (int l = 0; l < c->dim; ++l) nsp = std::max(nsp, p.ltab[l][0] == p.ltab[l][1] ? 1 : 2);
     if (!s.ok || slab_smem(ncp, nbp, ntp, fmt, nsp) > (size_t)dyn_max ||
         slab_smem(ncl, nbl, ntl, fmt) > (size_t)dyn_max) {
       rest.push_back(k);

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
   const int N = n[0] * n[1] * n[2];
   const long long base =
       (interior ? pt.ioff : pt.off) + (long long)l * N + (long long)blockIdx.z * rhs_stride;
-  const unsigned bs = b_slots(pt.tab[0], pt.tab[1], pt.tab[2]);
+  const unsigned bs = b_slots(pt.ltab[l][0], pt.ltab[l][1], pt.ltab[l][2]);
 
   // stage the B operands (prebuilt in the canonical layout) with TMA bulk
   // copies while the threads zero the operand buffer
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
     for (int m = 0; m < 6; ++m) {
       if (!(first & (1u << m))) continue;
       const int nd = n[m % 3];
-      const long long off = tabs[pt.tab[m % 3]].tcB[FMT == 1][interior][m >= 3];
+      const long long off = tabs[pt.ltab[l][m % 3]].tcB[FMT == 1][interior][m >= 3];
       bulk_g2s(bm + bslot(bs, m) * bsz, tcpool + off,
                (uint32_t)(rup(nd, 16) * rup(nd, KSTEP) * (int)sizeof(T)), &tma_bar);
     }
@@ -159,11 +159,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
   const uint32_t tmem = tslot;
 
   // Lambda for this (patch, component)
-  const float cl = (float)(2.0 * pt.mu + pt.lam), mu = (float)pt.mu, hs = (float)pt.Hs;
-  const float c0 = (l == 0) ? cl : mu, c1 = (l == 1) ? cl : mu, c2 = (l == 2) ? cl : mu;
+  const float hs = (float)pt.lscale, shf = (float)pt.lshift;
+  const float c0 = (float)pt.lcf[l][0], c1 = (float)pt.lcf[l][1], c2 = (float)pt.lcf[l][2];
   const float *Dv[3];
   for (int d = 0; d < 3; ++d) {
-    const Tab1D tb = tabs[pt.tab[d]];
+    const Tab1D tb = tabs[pt.ltab[l][d]];
     Dv[d] = fpool + (interior ? tb.Di : tb.D);
   }
 
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
           float x = __uint_as_float(raw[w][jj]);
           if (m == 2) {   // element r~(a1 = b, a2 = c, a3 = j): scale by Lambda^{-1}
             float lam = (dim == 3) ? lb + c2 * Dv[2][j] : c0 * Dv[0][b] + c1 * Dv[1][c];
-            if (!interior) lam = hs * (lam + 1.f);
+            if (!interior) lam = hs * (lam + shf);
             x = __fdividef(x, lam);
           }
           if (m == 5) s[base + line + (long long)n[0] * n[1] * j] = f32_to_f64(x);
@@ -255,7 +255,9 @@ struct TcNeed { int cap, bsz, tcols, nslot; bool ok; };
 
 static TcNeed tc_need(const DevPatch &p, int interior, int fmt) {
   const int kstep = (fmt == 2) ? 8 : 16, t16 = (fmt == 2) ? 4 : 8;
-  TcNeed t{0, 0, 32, (int)(b_slots(p.tab[0], p.tab[1], p.tab[2]) >> 24), true};
+  TcNeed t{0, 0, 32, 1, true};
+  for (int l = 0; l < 3; ++l)
+    t.nslot = std::max(t.nslot, (int)(b_slots(p.ltab[l][0], p.ltab[l][1], p.ltab[l][2]) >> 24));
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = interior ? p.ni[d] : p.n[d];
   for (int d = 0; d < 3; ++d) {

@@ -145,6 +145,8 @@ __global__ void k_basis(Tab1D *tabs, int ntab, double *pool) {
 }
 
 // K_hat_ij = sum_q w b_i' b_j',  M_hat_ij = sum_q w b_i b_j (dense n x n).
+// Geometry-inclusion tables (wK, wM >= 0) weight the points by the fitted
+// factors: K~_ij = sum_q w nu_q b_i' b_j',  M~_ij = sum_q w beta_q b_i b_j.
 __global__ void k_kmass(Tab1D *tabs, int ntab, double *pool) {
   int t = blockIdx.y;
   if (t >= ntab) return;
@@ -159,11 +161,13 @@ __global__ void k_kmass(Tab1D *tabs, int ntab, double *pool) {
     for (int e = elo; e <= ehi; ++e)
       for (int g = 0; g < ng; ++g) {
         int q = e * ng + g;
-        double w = pool[T.qw + q];
+        const double w = pool[T.qw + q];
+        const double wk = T.wK >= 0 ? w * pool[T.wK + q] : w;
+        const double wm = T.wM >= 0 ? w * pool[T.wM + q] : w;
         const double *v = pool + T.val + (long long)q * ng;
         const double *d = pool + T.der + (long long)q * ng;
-        k += w * d[i - e] * d[j - e];
-        m += w * v[i - e] * v[j - e];
+        k += wk * d[i - e] * d[j - e];
+        m += wm * v[i - e] * v[j - e];
       }
   }
   pool[T.K + idx] = k;
@@ -448,31 +452,46 @@ __global__ void k_small_inv(double *A, int nm, int count, int *flag) {
 }
 
 // ------------------------------------------------------------ host entry
-afi_status build_1d_tables(afi_ctx *c) {
-  const int nt = (int)c->htab.size();
-  launch(k_knots_quad, nt, 64, 0, 0, c->tabs, nt, c->dpool);
-  AFI_LAUNCH_CHECK();
+// Tables [t0, t1): knots, Gauss rules and basis tables (basis = true; the
+// geometry-inclusion tables share those of their base table), univariate
+// matrices, generalised eigenpairs (full and interior pencils), padded and
+// banded copies, and the low-precision mirrors of the whole pool.
+afi_status build_1d_tables_range(afi_ctx *c, int t0, int t1, bool basis) {
+  const int nt = t1 - t0;
+  if (nt <= 0) return AFI_OK;
+  Tab1D *tb = c->tabs + t0;
   int maxq = 1, maxn = 1;
-  for (auto &t : c->htab) { maxq = std::max(maxq, t.nq); maxn = std::max(maxn, t.n); }
-  launch(k_basis, dim3((maxq + 127) / 128, nt), 128, 0, 0, c->tabs, nt, c->dpool);
-  AFI_LAUNCH_CHECK();
-  launch(k_kmass, dim3((maxn * maxn + 127) / 128, nt), 128, 0, 0, c->tabs, nt, c->dpool);
+  for (int t = t0; t < t1; ++t) {
+    maxq = std::max(maxq, c->htab[t].nq);
+    maxn = std::max(maxn, c->htab[t].n);
+  }
+  if (basis) {
+    launch(k_knots_quad, nt, 64, 0, 0, tb, nt, c->dpool);
+    AFI_LAUNCH_CHECK();
+    launch(k_basis, dim3((maxq + 127) / 128, nt), 128, 0, 0, tb, nt, c->dpool);
+    AFI_LAUNCH_CHECK();
+  }
+  launch(k_kmass, dim3((maxn * maxn + 127) / 128, nt), 128, 0, 0, tb, nt, c->dpool);
   AFI_LAUNCH_CHECK();
   size_t smem = 3ull * maxn * maxn * sizeof(double);
   AFI_CUDA(cudaFuncSetAttribute(k_geneig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  launch(k_geneig, nt, 256, smem, 0, c->tabs, nt, c->dpool, 0, c->dflag);
+  launch(k_geneig, nt, 256, smem, 0, tb, nt, c->dpool, 0, c->dflag);
   AFI_LAUNCH_CHECK();
-  launch(k_geneig, nt, 256, smem, 0, c->tabs, nt, c->dpool, 1, c->dflag);
+  launch(k_geneig, nt, 256, smem, 0, tb, nt, c->dpool, 1, c->dflag);
   AFI_LAUNCH_CHECK();
   int h = 0;
   AFI_CUDA(cudaMemcpy(&h, c->dflag, sizeof(int), cudaMemcpyDeviceToHost));
   if (h) { set_error("univariate mass pencil not positive definite"); return AFI_ESINGULAR; }
-  launch(k_pad_u, dim3(16, nt), 256, 0, 0, c->tabs, nt, c->dpool);
-  launch(k_band, dim3(16, nt), 256, 0, 0, c->tabs, nt, c->dpool);
+  launch(k_pad_u, dim3(16, nt), 256, 0, 0, tb, nt, c->dpool);
+  launch(k_band, dim3(16, nt), 256, 0, 0, tb, nt, c->dpool);
   // low-precision copies of the eigenvectors: the pools mirror the FP64 pool
   launch(k_to_low, (unsigned)((c->dpool_n + 255) / 256), 256, 0, 0, c->dpool, c->fpool, c->bpool, c->dpool_n);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
+}
+
+afi_status build_1d_tables(afi_ctx *c) {
+  return build_1d_tables_range(c, 0, c->nbase_tab, true);
 }
 
 // Ainv = A^{-1} for SPD A (n x n); scratch holds n*n + n doubles.  A is

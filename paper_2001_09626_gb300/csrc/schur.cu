@@ -60,14 +60,13 @@ __device__ __forceinline__ void load_meta(PsMeta<T> &m, const DevPatch *P, const
     m.zo = (dim == 3) ? 1 : 0;
     m.off = pt.off + (long long)l * pt.N;
     m.ioff = pt.ioff + (long long)l * pt.Ni;
-    const Tab1D &tb = tabs[pt.tab[d]];
+    const Tab1D &tb = tabs[pt.ltab[l][d]];
     m.Mb = tpool + tb.Mb;
     m.Kb = tpool + tb.Kb;
-    const T cl = (T)(2.0 * pt.mu + pt.lam), mu = (T)pt.mu;
-    m.cf0 = (l == 0) ? cl : mu;
-    m.cf1 = (l == 1) ? cl : mu;
-    m.cf2 = (l == 2) ? cl : mu;
-    m.hs = (T)pt.Hs;
+    m.cf0 = (T)pt.lcf[l][0];
+    m.cf1 = (T)pt.lcf[l][1];
+    m.cf2 = (T)pt.lcf[l][2];
+    m.hs = (T)pt.lscale;
   }
   __syncthreads();
 }
@@ -100,12 +99,15 @@ constexpr int kOB = 4;   // consecutive outputs along the pass direction per thr
 //   PASS 3 (direction 3): t1 = M3 o + c3 K3 t2 (the last pass in 3D).
 // The last pass writes, for CALL 0, the interior entries of A_hat [theta; 0]
 // to rint (compact, FP64) and, for CALL 1, y = H^{d-2} (A_hat v) on the
-// shell and 0 inside.
+// shell and 0 inside.  With the geometry-inclusion solvers (dS non-null, the
+// per-dof D_S^{1/2} of eq. 5.13) theta enters as D_S^{1/2} theta and the
+// shell output leaves times D_S^{1/2}; the tables are then those of A~_l,
+// with unit coefficients and unit scale.
 template <typename T, int PC, int PASS, int CALL>
 __global__ void __launch_bounds__(256) k_ps_band(const DevPatch *P, const Tab1D *tabs, const T *tpool,
                                                  int dim, const double *t, const double *vint, T *O,
                                                  T *T1, T *T2, double *rint, double *y,
-                                                 const double *gate) {
+                                                 const double *dS, const double *gate) {
   if (gate && *gate == 0.0) return;   // inactive MINRES iteration
   constexpr int d = (PASS == 0) ? 0 : (PASS == 3 ? 2 : 1);
   __shared__ PsMeta<T> m;
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(256) k_ps_band(const DevPatch *P, const Tab1D 
     const long long at = base + j * stride;
     if (PASS == 0) {
       const int a1 = (d == 0) ? j : i1;
-      if (shell_node(m, a1, i2, i3, dim)) wa[w] = in64<T>(t[at]);
+      if (shell_node(m, a1, i2, i3, dim)) wa[w] = in64<T>(dS ? t[at] * dS[at] : t[at]);
       else if (CALL == 1) wa[w] = in64<T>(-vint[interior_at(m, a1, i2, i3)]);
     } else {
       wa[w] = sa[at];
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(256) k_ps_band(const DevPatch *P, const Tab1D 
     if (CALL == 0) {
       if (!sh) rint[interior_at(m, a1, a2, a3)] = out64(val);
     } else {
-      y[at] = sh ? out64(m.hs * val) : 0.0;
+      y[at] = sh ? (dS ? out64(m.hs * val) * dS[at] : out64(m.hs * val)) : 0.0;
     }
   }
 }
@@ -183,17 +185,18 @@ static void ahat_passes(afi_ctx *c, const double *t, const double *vint, T *O, T
   const Tab1D *tabs = c->tabs;
   const T *tp = SPool<T>::get(c);
   const double *gate = c->gate;
+  const double *dS = c->geo ? c->geo_dS : nullptr;
   // groups per tensor <= N / n_d * ceil(n_d / kOB) <= max_N / kOB + max_N / min(n)
   int gmax = 1;
   for (auto &q : c->hp)
     for (int d = 0; d < c->dim; ++d)
       gmax = std::max(gmax, q.N / q.n[d] * ((q.n[d] + kOB - 1) / kOB));
   const dim3 g((gmax + 255) / 256, c->npatch * c->dim);
-  launch(k_ps_band<T, PC, 0, CALL>, g, 256, 0, st, P, tabs, tp, c->dim, t, vint, O, T1, T2, rint, y, gate);
-  launch(k_ps_band<T, PC, 1, CALL>, g, 256, 0, st, P, tabs, tp, c->dim, t, vint, O, T1, T2, rint, y, gate);
+  launch(k_ps_band<T, PC, 0, CALL>, g, 256, 0, st, P, tabs, tp, c->dim, t, vint, O, T1, T2, rint, y, dS, gate);
+  launch(k_ps_band<T, PC, 1, CALL>, g, 256, 0, st, P, tabs, tp, c->dim, t, vint, O, T1, T2, rint, y, dS, gate);
   if (c->dim == 3) {
-    launch(k_ps_band<T, PC, 2, CALL>, g, 256, 0, st, P, tabs, tp, c->dim, t, vint, O, T1, T2, rint, y, gate);
-    launch(k_ps_band<T, PC, 3, CALL>, g, 256, 0, st, P, tabs, tp, c->dim, t, vint, O, T1, T2, rint, y, gate);
+    launch(k_ps_band<T, PC, 2, CALL>, g, 256, 0, st, P, tabs, tp, c->dim, t, vint, O, T1, T2, rint, y, dS, gate);
+    launch(k_ps_band<T, PC, 3, CALL>, g, 256, 0, st, P, tabs, tp, c->dim, t, vint, O, T1, T2, rint, y, dS, gate);
   }
 }
 

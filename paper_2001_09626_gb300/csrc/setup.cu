@@ -178,8 +178,15 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     set_error("invalid options");
     return AFI_EINVAL;
   }
+  if ((opt->variant & AFI_VARIANT_GEO) &&
+      (opt->variant & (AFI_VARIANT_LOCAL_ONLY | AFI_VARIANT_EXACT))) {
+    set_error("AFI_VARIANT_GEO needs the geometry and excludes AFI_VARIANT_LOCAL_ONLY and "
+              "AFI_VARIANT_EXACT");
+    return AFI_EINVAL;
+  }
   c->dim = D;
   c->npatch = NP;
+  c->geo = (opt->variant & AFI_VARIANT_GEO) != 0;
   c->nm = (D == 3) ? 6 : 3;
   c->opt = *opt;
   cudaGetDevice(&c->device);
@@ -208,6 +215,22 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     T.Uip = take((long long)T.ni * T.ldi); T.Uipt = take((long long)T.ni * T.ldi);
     T.Kb = take((long long)(2 * T.p + 1) * T.n); T.Mb = take((long long)(2 * T.p + 1) * T.n);
     T.Uf = T.U; T.Uif = T.Ui; T.Ub = T.U; T.Uib = T.Ui;   // low-precision pools mirror offsets
+    T.wK = T.wM = -1;
+    c->htab.push_back(T);
+    return (int)c->htab.size() - 1;
+  };
+  // a geometry-inclusion table: the knots, Gauss rule and basis tables of its
+  // base table, its own weights, matrices, eigenpairs and copies
+  auto make_geo_tab = [&](int base) {
+    Tab1D T = c->htab[base];
+    T.K = take((long long)T.n * T.n); T.M = take((long long)T.n * T.n);
+    T.U = take((long long)T.n * T.n); T.D = take(T.n);
+    T.Ui = take((long long)T.ni * T.ni); T.Di = take(T.ni);
+    T.Up = take((long long)T.n * T.ld); T.Upt = take((long long)T.n * T.ld);
+    T.Uip = take((long long)T.ni * T.ldi); T.Uipt = take((long long)T.ni * T.ldi);
+    T.Kb = take((long long)(2 * T.p + 1) * T.n); T.Mb = take((long long)(2 * T.p + 1) * T.n);
+    T.Uf = T.U; T.Uif = T.Ui; T.Ub = T.U; T.Uib = T.Ui;
+    T.wK = take(T.nq); T.wM = take(T.nq);
     c->htab.push_back(T);
     return (int)c->htab.size() - 1;
   };
@@ -226,6 +249,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     }
   }
   if (D == 2) dummy = make_tab(0, 0);
+  c->nbase_tab = (int)c->htab.size();
 
   // ---- patch descriptors
   long long off = 0, ioff = 0, soff = 0, qoff = 0, xoff = 0;
@@ -261,6 +285,28 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     c->max_N = std::max(c->max_N, P.N);
     for (int d = 0; d < D; ++d) c->max_n = std::max(c->max_n, P.n[d]);
   }
+  // local-solver descriptors per (patch, component): the plain parametric
+  // tables and coefficients (eqs. 5.6, 5.7), or one geometry-inclusion table
+  // per (patch, component, direction) with unit coefficients (eqs. 5.12,
+  // 5.13); shift and scale follow once H is known
+  long long qlo = 0;
+  for (int k = 0; k < NP; ++k) {
+    DevPatch &P = c->hp[k];
+    P.qloff = qlo;
+    qlo += P.nq[0] + P.nq[1] + P.nq[2];
+    for (int l = 0; l < 3; ++l)
+      for (int d = 0; d < 3; ++d) {
+        if (c->geo && l < D && d < D) {
+          P.ltab[l][d] = make_geo_tab(P.tab[d]);
+          P.lcf[l][d] = 1.0;
+        } else {
+          P.ltab[l][d] = P.tab[d];
+          P.lcf[l][d] = c->geo ? 1.0 : ((l == d) ? 2.0 * P.mu + P.lam : P.mu);
+        }
+      }
+    P.lshift = 1.0;
+    P.lscale = 1.0;
+  }
   if (off >= (1LL << 31)) { set_error("n_dof exceeds 2^31"); return AFI_EINVAL; }
   c->n_dof = (long)off;
   c->n_int = (long)ioff;
@@ -285,18 +331,32 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   AFI_TRY(fd_prepare(c));
   AFI_TRY(fd_tc_prepare(c));
   AFI_TRY(build_1d_tables(c));
-  AFI_TRY(fd_tc_tables(c));
+  if (!c->geo) AFI_TRY(fd_tc_tables(c));   // geometry inclusion: after its tables exist
   AFI_CUDA(cudaDeviceSynchronize());
   c->t_fd_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tf0).count();
   launch(k_patch_H, NP, 256, 0, 0, c->patches, c->ctrl, D);
   AFI_LAUNCH_CHECK();
   AFI_CUDA(cudaMemcpy(c->hp.data(), c->patches, NP * sizeof(DevPatch), cudaMemcpyDeviceToHost));
+  for (auto &P : c->hp) {   // Lambda = lscale (sum_m lcf D_m + lshift)
+    P.lshift = c->geo ? 1.0 / (P.H * P.H) : 1.0;
+    P.lscale = c->geo ? 1.0 : P.Hs;
+  }
+  AFI_CUDA(cudaMemcpy(c->patches, c->hp.data(), NP * sizeof(DevPatch), cudaMemcpyHostToDevice));
   if (!(opt->variant & AFI_VARIANT_LOCAL_ONLY)) {
     AFI_TRY(dalloc(c, (void **)&c->qgeo, (size_t)(D * D + 1) * qoff * sizeof(double)));
     AFI_TRY(compute_geometry(c));
     AFI_TRY(dalloc(c, (void **)&c->stencil, (size_t)soff * sizeof(double)));
     AFI_CUDA(cudaMemset(c->stencil, 0, (size_t)soff * sizeof(double)));   // padded nodes stay 0
     AFI_TRY(assemble_stiffness(c));
+    if (c->geo) {   // local-solver setup: the fit, its tables, the scalings
+      AFI_CUDA(cudaDeviceSynchronize());
+      const auto tg0 = std::chrono::steady_clock::now();
+      AFI_TRY(geo_setup(c));
+      AFI_TRY(fd_tc_tables(c));
+      AFI_CUDA(cudaDeviceSynchronize());
+      c->t_fd_setup_ms +=
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tg0).count();
+    }
     if (!(opt->variant & AFI_VARIANT_STENCIL_F64)) AFI_TRY(stencil_to_pairs(c));
   } else {
     c->nqp = 0;
@@ -538,7 +598,7 @@ void free_context(afi_ctx *c) {
                   c->tcsplit[1][0].d_plane, c->tcsplit[1][0].d_line, c->tcsplit[1][1].d_plane,
                   c->tcsplit[1][1].d_line, c->prow_coef, c->row_cp, c->row_cv, c->ps_buf,
                   c->ps_rint, c->ps_vint, c->xsplit, c->stencil2, c->ex_Kinv, c->ex_AIIinv,
-                  c->ex_koff, c->ex_aoff};
+                  c->ex_koff, c->ex_aoff, c->geo_dA, c->geo_dS, c->geo_tmp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);
