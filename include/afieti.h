@@ -238,7 +238,14 @@ afi_status fd_apply(afi_ctx *ctx, int interior, const double *r_dev, double *s_d
  * (Section 4).  f_dev, u_dev: [nrhs][n_dof]; lambda_dev: [nrhs][n_c] or NULL.
  * The call returns when the solve has finished (the host polls the
  * convergence flag).  info may be NULL.  Returns AFI_ENOT_CONVERGED if maxit
- * was reached (u is still the last iterate's recovery). */
+ * was reached (u is still the last iterate's recovery).
+ * nrhs > 1: the right-hand sides are solved in batches of up to 8 whose
+ * MINRES recurrences run in lockstep, sharing one batched stiffness launch
+ * per iteration (each solution is bitwise the one a separate call gives);
+ * info then holds the largest iteration count and residuals over all
+ * right-hand sides, the summed solve time and the number of FP64 restarts.
+ * The first multi-right-hand-side solve of a context allocates 8 sets of
+ * MINRES vectors (96 (n_dof + n_c) doubles). */
 afi_status ieti_solve(afi_ctx *ctx, const double *f_dev, double *u_dev, double *lambda_dev,
                       int nrhs, afi_info *info, void *stream);
 
@@ -265,6 +272,18 @@ afi_status afi_load_vector(afi_ctx *ctx, const double *c_dev, double *f_dev, voi
  * y_dev (lengths as listed there).  Stream-ordered, asynchronous. */
 afi_status afi_apply(afi_ctx *ctx, afi_operator op, const double *x_dev, double *y_dev,
                      void *stream);
+
+/* The same operator applied to nrhs vectors stacked in x_dev ([nrhs][input
+ * length]) into y_dev ([nrhs][output length]).  AFI_OP_STIFFNESS runs the
+ * batched double-FP32 stencil kernel on up to 8 vectors per launch (each
+ * coefficient streamed once for all of them; bitwise the same results as
+ * separate applications) when the pair copy exists, FP64 launches
+ * otherwise; AFI_OP_PA_INV is one batched FD launch; the other operators
+ * are applied one vector after the other.  (The batching has no
+ * counterpart in the paper: it serves several right-hand sides, eqs. 3.1,
+ * 4.7, 4.9.)  Errors as afi_apply, AFI_EINVAL for nrhs < 1. */
+afi_status afi_apply_batch(afi_ctx *ctx, afi_operator op, const double *x_dev, double *y_dev,
+                           int nrhs, void *stream);
 
 /* Change the local-solver arithmetic of an existing context (the low
  * precision copies of the eigenvectors are built at setup). */

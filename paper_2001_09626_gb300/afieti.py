@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": AFI_FD_FP64, "fp32": AFI_FD_FP32, "tf32": AFI_FD_TF32, "bf
 EXPORTED = ["af_ieti_setup", "fd_apply", "ieti_solve", "ieti_solve_adjoint", "afi_lame_grad",
             "afi_load_vector", "afi_apply", "afi_set_precision", "afi_sizes", "afi_memory",
             "af_ieti_destroy", "afi_status_string", "afi_last_error", "afi_kernel_launches",
-            "afi_fd_apply_static", "afi_selftest_bounded_wait"]
+            "afi_fd_apply_static", "afi_selftest_bounded_wait", "afi_apply_batch"]
 
 
 class afi_problem(C.Structure):
@@ -78,6 +78,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
     lib.afi_lame_grad.argtypes = [vp, dp, dp, dp, vp]
     lib.afi_load_vector.argtypes = [vp, dp, dp, vp]
     lib.afi_apply.argtypes = [vp, ip, dp, dp, vp]
+    lib.afi_apply_batch.argtypes = [vp, ip, dp, dp, ip, vp]
     lib.afi_set_precision.argtypes = [vp, ip]
     lib.afi_sizes.argtypes = [vp, C.POINTER(C.c_long), C.POINTER(C.c_long)]
     lib.afi_memory.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
@@ -217,6 +218,11 @@ def afi_load_vector(ctx, coef, f, stream=None):
 def afi_apply(ctx, op, x, y, stream=None):
     return _check(load().afi_apply(C.c_void_p(ctx), int(op), _ptr(x), _ptr(y), _stream(stream)),
                   "afi_apply")
+
+
+def afi_apply_batch(ctx, op, x, y, nrhs, stream=None):
+    return _check(load().afi_apply_batch(C.c_void_p(ctx), int(op), _ptr(x), _ptr(y), int(nrhs),
+                                         _stream(stream)), "afi_apply_batch")
 
 
 def afi_set_precision(ctx, prec):

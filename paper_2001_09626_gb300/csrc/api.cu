@@ -1,6 +1,8 @@
 // extern "C" entry points declared in include/afieti.h.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace afi {
 const char *last_error_cstr();
 }
@@ -52,13 +54,33 @@ static afi_status solve_many(afi_ctx *c, const double *f, double *u, double *lam
                              afi_info *info, void *stream) {
   if (!c || !f || !u || nrhs < 1) { set_error("solve: invalid argument"); return AFI_EINVAL; }
   if (!has_operator(c)) return AFI_EINVAL;
+  // batches of up to kMaxRhs right-hand sides solved in lockstep (one
+  // stiffness pass per iteration for the whole batch); info aggregates the
+  // batches: largest iteration count and residuals, summed solve time
   afi_status worst = AFI_OK;
-  for (int j = 0; j < nrhs; ++j) {
-    afi_status st = solve_one(c, f + (long long)j * c->n_dof, u + (long long)j * c->n_dof,
-                              lam ? lam + (long long)j * c->n_c : nullptr, info, as_stream(stream));
-    if (st == AFI_EBREAKDOWN || st == AFI_ECUDA || st == AFI_EINVAL || st == AFI_ENOMEM) return st;
+  afi_info agg{};
+  for (int j = 0; j < nrhs; j += kMaxRhs) {
+    const int nb = std::min(kMaxRhs, nrhs - j);
+    afi_info bi{};
+    const double *fj = f + (long long)j * c->n_dof;
+    double *uj = u + (long long)j * c->n_dof;
+    double *lj = lam ? lam + (long long)j * c->n_c : nullptr;
+    afi_status st = nb == 1 ? solve_one(c, fj, uj, lj, &bi, as_stream(stream))
+                            : solve_multi(c, fj, uj, lj, nb, &bi, as_stream(stream));
+    agg.iters = std::max(agg.iters, bi.iters);
+    agg.relres_est = std::max(agg.relres_est, bi.relres_est);
+    agg.relres_true = std::max(agg.relres_true, bi.relres_true);
+    agg.t_setup_ms = bi.t_setup_ms;
+    agg.t_fd_setup_ms = bi.t_fd_setup_ms;
+    agg.t_solve_ms += bi.t_solve_ms;
+    agg.fp64_restarts += bi.fp64_restarts;
+    if (st == AFI_EBREAKDOWN || st == AFI_ECUDA || st == AFI_EINVAL || st == AFI_ENOMEM) {
+      if (info) *info = agg;
+      return st;
+    }
     if (st != AFI_OK) worst = st;
   }
+  if (info) *info = agg;
   return worst;
 }
 
@@ -101,6 +123,40 @@ afi_status afi_apply(afi_ctx *c, afi_operator op, const double *x, double *y, vo
     case AFI_OP_SADDLE: return op_saddle(c, x, y, s);
     default: set_error("afi_apply: unknown operator"); return AFI_EINVAL;
   }
+}
+
+static long op_in_len(const afi_ctx *c, afi_operator op) {
+  switch (op) {
+    case AFI_OP_BT: case AFI_OP_PCHI: case AFI_OP_PS: return c->n_c;
+    case AFI_OP_PRECOND: case AFI_OP_SADDLE: return c->n_dof + c->n_c;
+    default: return c->n_dof;
+  }
+}
+
+static long op_out_len(const afi_ctx *c, afi_operator op) {
+  switch (op) {
+    case AFI_OP_B: case AFI_OP_PCHI: case AFI_OP_PS: return c->n_c;
+    case AFI_OP_PRECOND: case AFI_OP_SADDLE: return c->n_dof + c->n_c;
+    default: return c->n_dof;
+  }
+}
+
+afi_status afi_apply_batch(afi_ctx *c, afi_operator op, const double *x, double *y, int nrhs,
+                           void *stream) {
+  if (!c || !x || !y || nrhs < 1) { set_error("afi_apply_batch: invalid argument"); return AFI_EINVAL; }
+  cudaStream_t s = as_stream(stream);
+  const long ni = op_in_len(c, op), no = op_out_len(c, op);
+  if (op == AFI_OP_STIFFNESS) {
+    if (!has_operator(c)) return AFI_EINVAL;
+    for (int j = 0; j < nrhs; j += kMaxRhs)
+      AFI_TRY(op_stiffness_multi(c, x + (long long)j * ni, ni, y + (long long)j * no, no,
+                                 std::min(kMaxRhs, nrhs - j), s));
+    return AFI_OK;
+  }
+  if (op == AFI_OP_PA_INV && !c->exact) return fd_run(c, 0, x, y, s, nrhs);
+  for (int j = 0; j < nrhs; ++j)
+    AFI_TRY(afi_apply(c, op, x + (long long)j * ni, y + (long long)j * no, stream));
+  return AFI_OK;
 }
 
 afi_status afi_set_precision(afi_ctx *c, afi_fd_precision prec) {

@@ -186,6 +186,8 @@ struct afi_ctx {
   float2 *stencil2 = nullptr;                 // row-compressed (hi, lo) FP32-pair copy, or null
   long long stencil2_n = 0;                   // its size in pairs
   float2 *xsplit = nullptr;                   // (hi, lo) FP32 pairs of the matvec input
+  float2 *xsplit_multi = nullptr;             // the same for up to kMaxRhs inputs
+  int mv_width = 0;                           // vectors per batched stiffness launch (0: not tuned)
   // EXACT local solvers (AFI_VARIANT_EXACT): dense per-patch inverses
   bool exact = false;
   double *ex_Kinv = nullptr, *ex_AIIinv = nullptr;   // (A + H^-2 M)^{-1}, A_II^{-1}
@@ -243,10 +245,20 @@ struct afi_ctx {
   afi::TcSplit tcsplit[2][2];        // [interior][bf16]
   long long graph_nodes = 0;
   int graph_prec = -1;
+  // several right-hand sides solved in lockstep (ieti_solve with nrhs > 1):
+  // per right-hand side MINRES vectors and scalars, the captured iterations
+  double *mws = nullptr;             // [kMaxRhs][kKrylov][n_dof + n_c]
+  double *mst = nullptr;             // [kMaxRhs][kStStride] scalars, then the any-active flag
+  double *host_mst = nullptr;        // pinned mirror of mst
+  void *mgraph_exec = nullptr;
+  int mgraph_nr = 0, mgraph_prec = -1;
+  long long mgraph_nodes = 0;
 };
 
 namespace afi {
 
+constexpr int kMaxRhs = 8;               // right-hand sides per lockstep solve / batched matvec
+constexpr int kStStride = 128;           // doubles of MINRES scalars per right-hand side
 constexpr int kSmallDoubles = 1 << 16;   // reduction scratch (partials + scalars)
 constexpr int kOpScratch = 5;            // operator scratch, in units of (n_dof + n_c)
 constexpr int kKrylov = 12;              // MINRES vectors of length n_dof + n_c
@@ -264,6 +276,11 @@ afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status stencil_to_pairs(afi_ctx *c);
 bool stiffness_has_pairs(const afi_ctx *c);
 afi_status op_stiffness_fp64(afi_ctx *c, const double *x, double *y, cudaStream_t s);
+afi_status op_stiffness_multi(afi_ctx *c, const double *x, long long xstride, double *y,
+                              long long ystride, int nr, cudaStream_t s);
+afi_status stiffness_multi_prepare(afi_ctx *c, cudaStream_t s);
+afi_status solve_multi(afi_ctx *c, const double *f, double *u, double *lam, int nr,
+                       afi_info *info, cudaStream_t s);
 // exact.cu (EXACT local solvers, Section 5.1)
 afi_status exact_setup(afi_ctx *c);
 afi_status exact_PA_inv(afi_ctx *c, const double *r, double *s, cudaStream_t st);

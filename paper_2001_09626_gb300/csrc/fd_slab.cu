@@ -555,7 +555,8 @@ SlabNeed slab_need(const DevPatch &p, int interior, int fmt, int dim) {
 size_t slab_smem(int cap, int bsz, int tcols, int fmt, int nslot = 2) {
   const int esz = (fmt == 2) ? 4 : 2;
   const size_t smem = (size_t)(rup(cap, 256) + nslot * rup(bsz, 256)) * esz + 1024;
-  const size_t floor_smem = (size_t)228 * 1024 * (size_t)tcols / 512 + 1024;
+  // at most 512 / tcols CTAs per SM (see tc_smem in fd_tc.cu)
+  const size_t floor_smem = (size_t)228 * 1024 * (size_t)tcols / 512 - 2048;
   return std::max(smem, floor_smem);
 }
 

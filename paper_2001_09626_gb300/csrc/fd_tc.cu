@@ -277,8 +277,10 @@ static TcNeed tc_need(const DevPatch &p, int interior, int fmt) {
 static size_t tc_smem(int cap, int bsz, int tcols, int nslot, int fmt) {
   const int esz = (fmt == 2) ? 4 : 2;
   size_t smem = (size_t)(tc::rup(cap, 256) + nslot * tc::rup(bsz, 256)) * esz + 1024;
-  // at most 512 / tcols CTAs per SM, so tensor-memory allocation never waits long
-  const size_t floor_smem = (size_t)228 * 1024 * (size_t)tcols / 512 + 1024;
+  // at most 512 / tcols CTAs per SM, so tensor-memory allocation never waits
+  // long: the SM's 228 KiB hold 512 / tcols CTAs of this size (with their
+  // 1 KiB reserve and static shared memory) but not one more
+  const size_t floor_smem = (size_t)228 * 1024 * (size_t)tcols / 512 - 2048;
   return std::max(smem, floor_smem);
 }
 

@@ -806,10 +806,11 @@ static MinresBufs minres_bufs(afi_ctx *c) {
   return M;
 }
 
-// Enqueue one MINRES iteration after t completed ones (roles rotate with t).
-static afi_status enqueue_iteration(afi_ctx *c, const MinresBufs &M, long t, cudaStream_t s) {
+// Enqueue one MINRES iteration after t completed ones (roles rotate with t),
+// recurrence scalars in st.
+static afi_status enqueue_iteration(afi_ctx *c, const MinresBufs &M, double *st, long t,
+                                    cudaStream_t s) {
   const long nt = c->n_dof + c->n_c;
-  double *st = c->small;
   double *r1 = M.B[t % 3], *r2 = M.B[(t + 1) % 3], *y = M.B[(t + 2) % 3];
   double *w1 = M.W[t % 2], *w2 = M.W[(t + 1) % 2];
   unsigned *cnt = reinterpret_cast<unsigned *>(c->small + kCounters);
@@ -849,7 +850,7 @@ static afi_status ensure_graph(afi_ctx *c, const MinresBufs &M) {
   const long long before = g_launches.load();
   AFI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   afi_status st = AFI_OK;
-  for (int i = 0; i < kGraphIters && st == AFI_OK; ++i) st = enqueue_iteration(c, M, i, s);
+  for (int i = 0; i < kGraphIters && st == AFI_OK; ++i) st = enqueue_iteration(c, M, c->small, i, s);
   cudaError_t e = cudaStreamEndCapture(s, &g);
   g_launches.fetch_sub(g_launches.load() - before);
   if (st != AFI_OK) { if (g) cudaGraphDestroy(g); return st; }
@@ -876,9 +877,9 @@ struct ExactStiffness {
 };
 
 // ||b - calA x||^2 with the FP64 stiffness into st[S_RES2]; hs refreshed
-static afi_status true_residual2(afi_ctx *c, const MinresBufs &M, double *hs, cudaStream_t s) {
+static afi_status true_residual2(afi_ctx *c, const MinresBufs &M, double *st, double *hs,
+                                 cudaStream_t s) {
   const long nt = c->n_dof + c->n_c;
-  double *st = c->small;
   {
     ExactStiffness ex(c);
     AFI_TRY(op_saddle(c, M.x, M.tmp, s));
@@ -893,10 +894,9 @@ static afi_status true_residual2(afi_ctx *c, const MinresBufs &M, double *hs, cu
 // MINRES from x = 0 on the right-hand side in M.b: r1 = r2 = b,
 // y = M^{-1} b, beta_1, ||b||^2, the recurrence scalars (estimate tolerance
 // tol_est, iteration cap maxit) and v = y / beta_1; hs refreshed
-static afi_status minres_start(afi_ctx *c, const MinresBufs &M, double tol_est, long maxit, double *hs,
-                               cudaStream_t s) {
+static afi_status minres_start(afi_ctx *c, const MinresBufs &M, double *st, double tol_est,
+                               long maxit, double *hs, cudaStream_t s) {
   const long nt = c->n_dof + c->n_c;
-  double *st = c->small;
   AFI_CUDA(cudaMemsetAsync(M.x, 0, nt * sizeof(double), s));
   AFI_CUDA(cudaMemsetAsync(M.W[0], 0, nt * sizeof(double), s));
   AFI_CUDA(cudaMemsetAsync(M.W[1], 0, nt * sizeof(double), s));
@@ -927,10 +927,10 @@ struct LoopResult {
 // the estimate kept falling: the iteration's stiffness rounding then sets a
 // floor, and the caller restarts with the FP64 stiffness.  force_stall
 // treats the first check as such a stall.
-static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, bool use_graph, double bnorm, bool stop_on_stall,
-                              bool force_stall, double *hs, cudaStream_t s) {
+static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, double *st, bool use_graph,
+                              double bnorm, bool stop_on_stall, bool force_stall, double *hs,
+                              cudaStream_t s) {
   LoopResult R;
-  double *st = c->small;
   const double tol = c->opt.tol;
   long t = 0;   // completed iterations (buffer roles)
   double last_fail = 0.0, last_est = 0.0;   // true residual and estimate at the last failed check
@@ -944,7 +944,7 @@ static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, bool use_graph, d
       g_launches.fetch_add(c->graph_nodes);
       t += kGraphIters;
     } else {
-      e = enqueue_iteration(c, M, t, s);
+      e = enqueue_iteration(c, M, st, t, s);
       if (e != AFI_OK) return fail(e);
       t += 1;
     }
@@ -955,7 +955,7 @@ static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, bool use_graph, d
     if (hs[S_FLAG] == 2.0) return fail(AFI_EBREAKDOWN);
     if (hs[S_FLAG] == 1.0) {
       // estimate converged at iteration itn: confirm with the true residual
-      e = true_residual2(c, M, hs, s);
+      e = true_residual2(c, M, st, hs, s);
       if (e != AFI_OK) return fail(e);
       R.relres_true = sqrt(hs[S_RES2]) / (bnorm > 0 ? bnorm : 1.0);
       R.checked_at = itn;
@@ -989,24 +989,17 @@ static LoopResult minres_loop(afi_ctx *c, const MinresBufs &M, bool use_graph, d
     if (itn >= (long)hs[S_MAXIT]) { R.status = AFI_ENOT_CONVERGED; break; }
   }
   if (R.checked_at != (long)hs[S_ITN]) {   // true residual of the final iterate
-    afi_status e = true_residual2(c, M, hs, s);
+    afi_status e = true_residual2(c, M, st, hs, s);
     if (e != AFI_OK) return fail(e);
     R.relres_true = sqrt(hs[S_RES2]) / (bnorm > 0 ? bnorm : 1.0);
   }
   return R;
 }
 
-// one right-hand side
-afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, afi_info *info,
-                     cudaStream_t s) {
-  const long n = c->n_dof, m = c->n_c, nt = n + m;
-  const MinresBufs M = minres_bufs(c);
-  cudaEvent_t e0, e1;
-  AFI_CUDA(cudaEventCreate(&e0));
-  AFI_CUDA(cudaEventCreate(&e1));
-  AFI_CUDA(cudaEventRecord(e0, s));
-  c->mv_exact = false;
-  // lambda_0 = G (G^T G)^{-1} R^T f and b = [f - B^T lambda_0; 0]
+// lambda_0 = G (G^T G)^{-1} R^T f into M.lam0 and b = [f - B^T lambda_0; 0]
+// into M.b (Section 4)
+static afi_status rhs_setup(afi_ctx *c, const MinresBufs &M, const double *f, cudaStream_t s) {
+  const long n = c->n_dof, m = c->n_c;
   if (m > 0) {
     AFI_TRY(op_Rt(c, f, gbuf(c, 0), s));
     AFI_TRY(op_dense_inv(c, gbuf(c, 0), gbuf(c, 1), s));
@@ -1017,42 +1010,13 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
     AFI_TRY(op_Bt_scaled(c, M.lam0, M.b, -1.0, true, false, s));
     AFI_CUDA(cudaMemsetAsync(M.b + n, 0, m * sizeof(double), s));
   }
-  double *hs = c->host_small;
-  const double tol = c->opt.tol;
-  AFI_TRY(minres_start(c, M, tol, c->opt.maxit, hs, s));
-  const double bnorm = sqrt(hs[S_BNORM2]);
-  const bool use_graph = c->opt.use_graph != 0;
-  if (use_graph) {
-    AFI_TRY(fd_tc_ready(c));   // no allocation or host copy during capture
-    AFI_TRY(ensure_graph(c, M));
-  }
-  const bool pairs = stiffness_has_pairs(c);
-  LoopResult R = minres_loop(c, M, use_graph, bnorm, pairs,
-                             pairs && (c->opt.variant & AFI_VARIANT_FORCE_RESTART), hs, s);
-  long iters = (long)hs[S_ITN];
-  int restarts = 0;
-  if (R.status == AFI_OK && R.stalled) {
-    // FP64 restart from the current iterate x0: solve calA d = b - calA x0
-    // with the FP64 stiffness (host-launched iterations), then x = x0 + d
-    AFI_CUDA(cudaMemcpyAsync(M.x0, M.x, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    AFI_CUDA(cudaMemcpyAsync(M.b, M.tmp, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));   // b - calA x0
-    c->mv_exact = true;
-    const double rnorm = R.relres_true * bnorm;
-    afi_status e = minres_start(c, M, tol * bnorm / (rnorm > 0 ? rnorm : 1.0),
-                                std::max(1L, (long)c->opt.maxit - iters), hs, s);
-    if (e == AFI_OK) {
-      R = minres_loop(c, M, false, bnorm, false, false, hs, s);
-      iters += (long)hs[S_ITN];
-      restarts = 1;
-    } else {
-      R.status = e;
-    }
-    c->mv_exact = false;
-    launch(k_add, nblk(nt), 256, 0, s, (const double *)M.x0, (const double *)M.x, M.x, nt);
-    AFI_LAUNCH_CHECK();
-  }
-  afi_status status = R.status;
-  // recovery: u = w - R (G^T G)^{-1} G^T B w, lambda = lambda_0 + chi
+  return AFI_OK;
+}
+
+// recovery: u = w - R (G^T G)^{-1} G^T B w, lambda = lambda_0 + chi
+static afi_status recover(afi_ctx *c, const MinresBufs &M, double *u, double *lam_out,
+                          cudaStream_t s) {
+  const long n = c->n_dof, m = c->n_c;
   AFI_CUDA(cudaMemcpyAsync(u, M.x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (m > 0) {
     AFI_TRY(op_B(c, M.x, M.tmp, s));
@@ -1064,6 +1028,66 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
       AFI_LAUNCH_CHECK();
     }
   }
+  return AFI_OK;
+}
+
+// FP64 restart from the iterate in M.x, whose residual b - calA x is in
+// M.tmp (reading 19 of the stopping rule): solve calA d = b - calA x with the
+// FP64 stiffness (host-launched iterations, scalars in c->small), then
+// x = x + d.  R is replaced by the restarted run's result; its iterations
+// are added to *iters.
+static afi_status fp64_restart(afi_ctx *c, const MinresBufs &M, double bnorm, LoopResult &R,
+                               long *iters, cudaStream_t s) {
+  const long nt = c->n_dof + c->n_c;
+  double *hs = c->host_small;
+  AFI_CUDA(cudaMemcpyAsync(M.x0, M.x, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AFI_CUDA(cudaMemcpyAsync(M.b, M.tmp, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  c->mv_exact = true;
+  const double rnorm = R.relres_true * bnorm;
+  afi_status e = minres_start(c, M, c->small, c->opt.tol * bnorm / (rnorm > 0 ? rnorm : 1.0),
+                              std::max(1L, (long)c->opt.maxit - *iters), hs, s);
+  if (e == AFI_OK) {
+    R = minres_loop(c, M, c->small, false, bnorm, false, false, hs, s);
+    *iters += (long)hs[S_ITN];
+  } else {
+    R.status = e;
+  }
+  c->mv_exact = false;
+  launch(k_add, nblk(nt), 256, 0, s, (const double *)M.x0, (const double *)M.x, M.x, nt);
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
+}
+
+// one right-hand side
+afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, afi_info *info,
+                     cudaStream_t s) {
+  const MinresBufs M = minres_bufs(c);
+  cudaEvent_t e0, e1;
+  AFI_CUDA(cudaEventCreate(&e0));
+  AFI_CUDA(cudaEventCreate(&e1));
+  AFI_CUDA(cudaEventRecord(e0, s));
+  c->mv_exact = false;
+  AFI_TRY(rhs_setup(c, M, f, s));
+  double *hs = c->host_small;
+  const double tol = c->opt.tol;
+  AFI_TRY(minres_start(c, M, c->small, tol, c->opt.maxit, hs, s));
+  const double bnorm = sqrt(hs[S_BNORM2]);
+  const bool use_graph = c->opt.use_graph != 0;
+  if (use_graph) {
+    AFI_TRY(fd_tc_ready(c));   // no allocation or host copy during capture
+    AFI_TRY(ensure_graph(c, M));
+  }
+  const bool pairs = stiffness_has_pairs(c);
+  LoopResult R = minres_loop(c, M, c->small, use_graph, bnorm, pairs,
+                             pairs && (c->opt.variant & AFI_VARIANT_FORCE_RESTART), hs, s);
+  long iters = (long)hs[S_ITN];
+  int restarts = 0;
+  if (R.status == AFI_OK && R.stalled) {
+    AFI_TRY(fp64_restart(c, M, bnorm, R, &iters, s));
+    restarts = 1;
+  }
+  afi_status status = R.status;
+  AFI_TRY(recover(c, M, u, lam_out, s));
   AFI_CUDA(cudaEventRecord(e1, s));
   AFI_CUDA(cudaEventSynchronize(e1));
   int tc_timeout = 0;   // set by a tensor-core or bulk-copy kernel whose bounded wait ran out
@@ -1077,6 +1101,304 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
     info->iters = (int)iters;
     info->relres_est = hs[S_REL];
     info->relres_true = R.relres_true;
+    info->t_setup_ms = c->t_setup_ms;
+    info->t_fd_setup_ms = c->t_fd_setup_ms;
+    info->t_solve_ms = ms;
+    info->fp64_restarts = restarts;
+  }
+  if (status == AFI_EBREAKDOWN) set_error("MINRES breakdown (non-finite or negative norm)");
+  if (status == AFI_ENOT_CONVERGED) set_error("MINRES reached maxit before the tolerance");
+  if (status == AFI_ETIMEOUT) set_error("a tensor-core or bulk-copy kernel timed out on a bounded wait");
+  return status;
+}
+
+
+// ------------------------------------------- several right-hand sides
+// ieti_solve with nrhs > 1 runs up to kMaxRhs MINRES recurrences in
+// lockstep: each right-hand side has its own vectors (c->mws) and scalars
+// (c->mst), and every iteration applies the stiffness to all of their
+// Lanczos vectors in one batched launch (op_stiffness_multi: the stencil is
+// streamed once for all of them); the rest of each iteration (multiplier
+// products, preconditioner, dots, updates) runs per right-hand side, gated
+// by that right-hand side's own active flag.  The buffer roles rotate with
+// the common iteration count t; a right-hand side that paused for a
+// true-residual check and then continues has its rotating buffers moved to
+// the roles of t (k_rotate_roles), so one captured graph serves all of them;
+// the host keeps, per right-hand side, the offset between the common index
+// its buffers are arranged for and its own iteration count.
+static MinresBufs multi_bufs(afi_ctx *c, int j) {
+  const long nt = c->n_dof + c->n_c;
+  double *V = c->mws + (long long)j * kKrylov * nt;
+  MinresBufs M;
+  M.b = V; M.x = V + nt; M.v = V + 2 * nt;
+  M.B[0] = V + 3 * nt; M.B[1] = V + 4 * nt; M.B[2] = V + 5 * nt;
+  M.W[0] = V + 6 * nt; M.W[1] = V + 7 * nt;
+  M.tA = V + 8 * nt; M.x0 = V + 9 * nt; M.tmp = V + 10 * nt; M.lam0 = V + 11 * nt;
+  return M;
+}
+
+static double *multi_st(afi_ctx *c, int j) { return c->mst + (long long)j * kStStride; }
+static double *multi_any(afi_ctx *c) { return c->mst + (long long)kMaxRhs * kStStride; }
+
+// any[0] = 1 if some right-hand side is active in this iteration
+__global__ void k_any_active(const double *mst, int nr, double *any) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0;
+  for (int j = 0; j < nr; ++j) a = fmax(a, mst[(long long)j * kStStride + S_ACTIVE]);
+  *any = a;
+}
+
+// new B[k] = old B[(k - d3) mod 3], new W[k] = old W[(k - d2) mod 2]
+__global__ void k_rotate_roles(double *B0, double *B1, double *B2, double *W0, double *W1, long n,
+                               int d3, int d2) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const double b[3] = {B0[i], B1[i], B2[i]}, w[2] = {W0[i], W1[i]};
+    B0[i] = b[(3 - d3) % 3];
+    B1[i] = b[(4 - d3) % 3];
+    B2[i] = b[(5 - d3) % 3];
+    W0[i] = w[(2 - d2) % 2];
+    W1[i] = w[(3 - d2) % 2];
+  }
+}
+
+// [A w + B^T P_chi chi ; P_chi B w] given A w already in y (eq. 4.7)
+static afi_status saddle_multipliers(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
+  const long n = c->n_dof;
+  if (c->n_c == 0) return AFI_OK;
+  double *m2 = c->ws + 4 * n + 2 * c->n_c, *m3 = m2 + c->n_c;
+  AFI_TRY(op_Pchi(c, x + n, m2, s));
+  AFI_TRY(op_B(c, x, m3, s));
+  AFI_TRY(op_Pchi(c, m3, y + n, s));
+  AFI_TRY(op_Bt(c, m2, y, true, false, s));
+  return AFI_OK;
+}
+
+// one lockstep iteration of nr recurrences after t completed ones
+static afi_status enqueue_iteration_multi(afi_ctx *c, int nr, long t, cudaStream_t s) {
+  const long nt = c->n_dof + c->n_c;
+  unsigned *cnt = reinterpret_cast<unsigned *>(c->small + kCounters);
+  struct GateScope {
+    afi_ctx *c;
+    GateScope(afi_ctx *cc, const double *g) : c(cc) { c->gate = g; }
+    ~GateScope() { c->gate = nullptr; }
+  };
+  for (int j = 0; j < nr; ++j) launch(k_iter_begin, 1, 1, 0, s, multi_st(c, j));
+  launch(k_any_active, 1, 32, 0, s, (const double *)c->mst, nr, multi_any(c));
+  {
+    GateScope g(c, multi_any(c));
+    const MinresBufs M0 = multi_bufs(c, 0);
+    const long long stride = (long long)kKrylov * nt;
+    AFI_TRY(op_stiffness_multi(c, M0.v, stride, M0.tA, stride, nr, s));
+  }
+  for (int j = 0; j < nr; ++j) {
+    const MinresBufs M = multi_bufs(c, j);
+    double *st = multi_st(c, j);
+    double *r1 = M.B[t % 3], *r2 = M.B[(t + 1) % 3], *y = M.B[(t + 2) % 3];
+    double *w1 = M.W[t % 2], *w2 = M.W[(t + 1) % 2];
+    GateScope g(c, st + S_ACTIVE);
+    AFI_TRY(saddle_multipliers(c, M.v, M.tA, s));
+    launch(k_y_upd1, kDotBlocks, 256, 0, s, (const double *)M.tA, y, (const double *)r1,
+           (const double *)M.v, nt, st, c->small + kPart, cnt);
+    launch(k_y_upd2, nblk(nt), 256, 0, s, y, (const double *)r2, nt, (const double *)st);
+    AFI_TRY(op_precond(c, y, r1, s));
+    launch(k_dot_active, kDotBlocks, 256, 0, s, (const double *)y, (const double *)r1, nt, st,
+           c->small + kPart, cnt + 1);
+    launch(k_minres_scalars, 1, 1, 0, s, st);
+    launch(k_w_upd, nblk(nt), 256, 0, s, M.v, (const double *)w1, (const double *)w2, w1, M.x,
+           (const double *)r1, nt, (const double *)st);
+  }
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
+}
+
+static afi_status ensure_multi_graph(afi_ctx *c, int nr) {
+  if (c->mgraph_exec && c->mgraph_prec == (int)c->opt.prec && c->mgraph_nr == nr) return AFI_OK;
+  cudaStream_t s = (cudaStream_t)c->cap_stream;
+  if (c->mgraph_exec) { cudaGraphExecDestroy((cudaGraphExec_t)c->mgraph_exec); c->mgraph_exec = nullptr; }
+  cudaGraph_t g = nullptr;
+  const long long before = g_launches.load();
+  AFI_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  afi_status st = AFI_OK;
+  for (int i = 0; i < kGraphIters && st == AFI_OK; ++i) st = enqueue_iteration_multi(c, nr, i, s);
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  g_launches.fetch_sub(g_launches.load() - before);
+  if (st != AFI_OK) { if (g) cudaGraphDestroy(g); return st; }
+  if (e != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(e)); return AFI_ECUDA; }
+  size_t nodes = 0;
+  cudaGraphGetNodes(g, nullptr, &nodes);
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(e)); return AFI_ECUDA; }
+  c->mgraph_exec = ex;
+  c->mgraph_nodes = (long long)nodes;
+  c->mgraph_prec = (int)c->opt.prec;
+  c->mgraph_nr = nr;
+  return AFI_OK;
+}
+
+static afi_status multi_alloc(afi_ctx *c) {
+  const long nt = c->n_dof + c->n_c;
+  if (!c->mws) AFI_TRY(dalloc(c, (void **)&c->mws, (size_t)kMaxRhs * kKrylov * nt * sizeof(double)));
+  if (!c->mst) {
+    AFI_TRY(dalloc(c, (void **)&c->mst, (size_t)(kMaxRhs + 1) * kStStride * sizeof(double)));
+    AFI_CUDA(cudaMemset(c->mst, 0, (size_t)(kMaxRhs + 1) * kStStride * sizeof(double)));
+  }
+  if (!c->host_mst)
+    AFI_CUDA(cudaMallocHost((void **)&c->host_mst, (size_t)kMaxRhs * kStStride * sizeof(double)));
+  return AFI_OK;
+}
+
+// nr (2 .. kMaxRhs) right-hand sides f_j = f + j n_dof in lockstep; u_j and
+// lambda_j (optional) likewise.  info: the largest iteration count and true
+// residual over the right-hand sides, the number of FP64 restarts.
+afi_status solve_multi(afi_ctx *c, const double *f, double *u, double *lam_out, int nr,
+                       afi_info *info, cudaStream_t s) {
+  const long n = c->n_dof, m = c->n_c;
+  if (nr < 2 || nr > kMaxRhs) { set_error("solve_multi: 2 <= nrhs <= 8 per batch"); return AFI_EINVAL; }
+  AFI_TRY(multi_alloc(c));
+  AFI_TRY(stiffness_multi_prepare(c, s));
+  cudaEvent_t e0, e1;
+  AFI_CUDA(cudaEventCreate(&e0));
+  AFI_CUDA(cudaEventCreate(&e1));
+  AFI_CUDA(cudaEventRecord(e0, s));
+  c->mv_exact = false;
+  const double tol = c->opt.tol;
+  const bool pairs = stiffness_has_pairs(c);
+  const bool force_stall = pairs && (c->opt.variant & AFI_VARIANT_FORCE_RESTART);
+  struct Run {
+    LoopResult R;
+    double bnorm = 0.0, last_fail = 0.0, last_est = 0.0;
+    bool done = false;
+    long lag = 0;   // (common index its buffers are arranged for) - (its own iteration count)
+  };
+  std::vector<Run> run(nr);
+  for (int j = 0; j < nr; ++j) {
+    const MinresBufs M = multi_bufs(c, j);
+    double *hs = c->host_mst + (long long)j * kStStride;
+    AFI_TRY(rhs_setup(c, M, f + (long long)j * n, s));
+    AFI_TRY(minres_start(c, M, multi_st(c, j), tol, c->opt.maxit, hs, s));
+    run[j].bnorm = sqrt(hs[S_BNORM2]);
+    if (hs[S_FLAG] == 2.0) { run[j].R.status = AFI_EBREAKDOWN; run[j].done = true; }
+    else if (hs[S_FLAG] != 0.0) {   // b = 0
+      run[j].R.converged = true;
+      run[j].done = true;
+      run[j].R.checked_at = 0;
+    }
+  }
+  const bool use_graph = c->opt.use_graph != 0;
+  if (use_graph) {
+    AFI_TRY(fd_tc_ready(c));
+    AFI_TRY(ensure_multi_graph(c, nr));
+  }
+  long t = 0;
+  auto all_done = [&]() {
+    for (auto &r : run)
+      if (!r.done) return false;
+    return true;
+  };
+  while (!all_done()) {
+    if (use_graph && t % kGraphIters == 0) {
+      if (cudaGraphLaunch((cudaGraphExec_t)c->mgraph_exec, s) != cudaSuccess) {
+        set_error("graph launch failed");
+        return AFI_ECUDA;
+      }
+      g_launches.fetch_add(c->mgraph_nodes);
+      t += kGraphIters;
+    } else {
+      AFI_TRY(enqueue_iteration_multi(c, nr, t, s));
+      t += 1;
+    }
+    AFI_CUDA(cudaMemcpyAsync(c->host_mst, c->mst, (size_t)nr * kStStride * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+    AFI_CUDA(cudaStreamSynchronize(s));
+    for (int j = 0; j < nr; ++j) {
+      Run &r = run[j];
+      if (r.done) continue;
+      const MinresBufs M = multi_bufs(c, j);
+      double *st = multi_st(c, j), *hs = c->host_mst + (long long)j * kStStride;
+      const long itn = (long)hs[S_ITN];
+      if (hs[S_FLAG] == 2.0) { r.R.status = AFI_EBREAKDOWN; r.done = true; continue; }
+      if (hs[S_FLAG] == 1.0) {
+        // estimate converged at iteration itn: confirm with the true residual
+        AFI_TRY(true_residual2(c, M, st, hs, s));
+        r.R.relres_true = sqrt(hs[S_RES2]) / (r.bnorm > 0 ? r.bnorm : 1.0);
+        r.R.checked_at = itn;
+        if (force_stall) { r.R.stalled = true; r.done = true; continue; }
+        if (r.R.relres_true <= tol) { r.R.converged = true; r.done = true; continue; }
+        const double est = hs[S_REL];
+        if (pairs && r.last_fail > 0.0 && est < 0.25 * r.last_est &&
+            r.R.relres_true > r.last_fail / 1.5) {
+          r.R.stalled = true;
+          r.done = true;
+          continue;
+        }
+        r.last_fail = r.R.relres_true;
+        r.last_est = est;
+        long extra = 5;
+        if (itn >= 5) {
+          const double rn = hs[kRelHist + itn % 8], r5 = hs[kRelHist + (itn - 5) % 8];
+          if (rn > 0.0 && r5 > 0.0) {
+            const double q = pow(rn / r5, 0.2);
+            if (q > 0.0 && q < 1.0) extra = (long)ceil(log(r.R.relres_true / tol) / (-log(q)));
+          }
+        }
+        extra = std::min(std::max(extra, 5L), 50L);
+        launch(k_set, 1, 1, 0, s, st, (int)S_NEXTCHECK, (double)(itn + extra));
+        launch(k_set, 1, 1, 0, s, st, (int)S_FLAG, 0.0);
+        // the data state of this right-hand side is that of itn own
+        // iterations, arranged for the common index itn + lag: move its
+        // rotating buffers to the roles of the common count t
+        const long shift = t - itn - r.lag;
+        r.lag = t - itn;
+        const int d3 = (int)((shift % 3 + 3) % 3), d2 = (int)((shift % 2 + 2) % 2);
+        if (d3 || d2)
+          launch(k_rotate_roles, (unsigned)std::min<long>(nblk(n + m), 8L * c->nsm), 256, 0, s,
+                 M.B[0], M.B[1], M.B[2], M.W[0], M.W[1], n + m, d3, d2);
+        AFI_LAUNCH_CHECK();
+      }
+      if (itn >= (long)hs[S_MAXIT]) { r.R.status = AFI_ENOT_CONVERGED; r.done = true; }
+    }
+  }
+  // final true residuals, FP64 restarts of stalled right-hand sides, recovery
+  int restarts = 0;
+  long max_it = 0;
+  double max_res = 0.0, max_est = 0.0;
+  afi_status status = AFI_OK;
+  for (int j = 0; j < nr; ++j) {
+    Run &r = run[j];
+    const MinresBufs M = multi_bufs(c, j);
+    double *st = multi_st(c, j), *hs = c->host_mst + (long long)j * kStStride;
+    AFI_CUDA(cudaMemcpyAsync(hs, st, kHostStats * sizeof(double), cudaMemcpyDeviceToHost, s));
+    AFI_CUDA(cudaStreamSynchronize(s));
+    long iters = (long)hs[S_ITN];
+    max_est = std::max(max_est, hs[S_REL]);
+    if ((r.R.status == AFI_OK || r.R.status == AFI_ENOT_CONVERGED) && r.R.checked_at != iters) {
+      AFI_TRY(true_residual2(c, M, st, hs, s));
+      r.R.relres_true = sqrt(hs[S_RES2]) / (r.bnorm > 0 ? r.bnorm : 1.0);
+    }
+    if (r.R.status == AFI_OK && r.R.stalled) {
+      AFI_TRY(fp64_restart(c, M, r.bnorm, r.R, &iters, s));
+      ++restarts;
+    }
+    if (r.R.status != AFI_OK && status == AFI_OK) status = r.R.status;
+    AFI_TRY(recover(c, M, u + (long long)j * n, lam_out ? lam_out + (long long)j * m : nullptr, s));
+    max_it = std::max(max_it, iters);
+    max_res = std::max(max_res, r.R.relres_true);
+  }
+  AFI_CUDA(cudaEventRecord(e1, s));
+  AFI_CUDA(cudaEventSynchronize(e1));
+  int tc_timeout = 0;
+  AFI_CUDA(cudaMemcpy(&tc_timeout, c->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  if (tc_timeout && status == AFI_OK) status = AFI_ETIMEOUT;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iters = (int)max_it;
+    info->relres_est = max_est;
+    info->relres_true = max_res;
     info->t_setup_ms = c->t_setup_ms;
     info->t_fd_setup_ms = c->t_fd_setup_ms;
     info->t_solve_ms = ms;

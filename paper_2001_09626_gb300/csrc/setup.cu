@@ -583,6 +583,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
 
 void free_context(afi_ctx *c) {
   if (c->graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->graph_exec);
+  if (c->mgraph_exec) cudaGraphExecDestroy((cudaGraphExec_t)c->mgraph_exec);
   if (c->cap_stream) cudaStreamDestroy((cudaStream_t)c->cap_stream);
   if (c->aux_stream) cudaStreamDestroy((cudaStream_t)c->aux_stream);
   if (c->ev_fork) cudaEventDestroy((cudaEvent_t)c->ev_fork);
@@ -598,10 +599,12 @@ void free_context(afi_ctx *c) {
                   c->tcsplit[1][0].d_plane, c->tcsplit[1][0].d_line, c->tcsplit[1][1].d_plane,
                   c->tcsplit[1][1].d_line, c->prow_coef, c->row_cp, c->row_cv, c->ps_buf,
                   c->ps_rint, c->ps_vint, c->xsplit, c->stencil2, c->ex_Kinv, c->ex_AIIinv,
-                  c->ex_koff, c->ex_aoff, c->geo_dA, c->geo_dS, c->geo_tmp};
+                  c->ex_koff, c->ex_aoff, c->geo_dA, c->geo_dS, c->geo_tmp, c->mws, c->mst,
+                  c->xsplit_multi};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);
+  if (c->host_mst) cudaFreeHost(c->host_mst);
 }
 
 }  // namespace afi

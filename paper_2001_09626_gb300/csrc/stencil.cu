@@ -94,6 +94,17 @@ __global__ void k_split_x(const double *__restrict__ x, float2 *__restrict__ xs,
   xs[i] = make_float2(hi, __double2float_rn(v - (double)hi));
 }
 
+// the same for gridDim.y vectors x_j = x + j xstride into xs + j n
+__global__ void k_split_x_multi(const double *__restrict__ x, long long xstride,
+                                float2 *__restrict__ xs, long n, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration(s)
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = x[(long long)blockIdx.y * xstride + i];
+  const float hi = __double2float_rn(v);
+  xs[(long long)blockIdx.y * n + i] = make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 // sum += a x in double-FP32; the rounding steps are spelled out so that no
 // contraction or reassociation can change them
 __device__ __forceinline__ void df_madd(float &sh, float &sl, float2 a, float2 x) {
@@ -210,11 +221,15 @@ struct RowsCfg {
   static constexpr int SMEM = NST * STAGE;
 };
 
-template <int DIM, int PC>
+// NR > 1: up to NR right-hand sides per launch (nrhs of them: x_j at
+// xs + j n_dof, y_j at y + j ystride); every coefficient pair brought into
+// shared memory serves all of them.
+template <int DIM, int PC, int NR>
 __global__ void __launch_bounds__(kRowsTN + 32) k_stencil_mv_rows(const DevPatch *P, const float2 *__restrict__ A2,
                                                                   const float2 *__restrict__ xs,
                                                                   double *__restrict__ y, const double *gate,
-                                                                  int *err) {
+                                                                  int *err, int nrhs, long ndof,
+                                                                  long long ystride) {
   using C = RowsCfg<DIM, PC>;
   constexpr int W = C::W, W3 = C::W3, NROW = C::NROW, NST = C::NST;
   if (gate && *gate == 0.0) return;   // inactive MINRES iteration
@@ -299,9 +314,11 @@ __global__ void __launch_bounds__(kRowsTN + 32) k_stencil_mv_rows(const DevPatch
   const bool act = tr < nr;
   const int rr = r0 + tr, i3 = rr / n2, i2 = rr - i3 * n2;
   const int N = pt.N;
-  float sh[DIM], sl[DIM];
+  float sh[NR][DIM], sl[NR][DIM];
 #pragma unroll
-  for (int l = 0; l < DIM; ++l) sh[l] = sl[l] = 0.0f;
+  for (int j = 0; j < NR; ++j)
+#pragma unroll
+    for (int l = 0; l < DIM; ++l) sh[j][l] = sl[j][l] = 0.0f;
   int k = 0;
   bool failed = false;
   for (int r = 0; r < NROW; ++r) {
@@ -323,17 +340,26 @@ __global__ void __launch_bounds__(kRowsTN + 32) k_stencil_mv_rows(const DevPatch
         // read at a clamped slot position
         const int j1 = i1 + o1 - PC;
         const bool in = j1 >= 0 && j1 < n1;
-        const float2 xv = in ? xm[j1] : make_float2(0.0f, 0.0f);
         const int at = min(max(((first * L.len[o1]) & 1) + dr * L.len[o1] + i1 - L.s[o1], 0), kSlot - 1);
+        float2 av[DIM];
 #pragma unroll
-        for (int l = 0; l < DIM; ++l) df_madd(sh[l], sl[l], st[(l * W + o1) * kSlot + at], xv);
+        for (int l = 0; l < DIM; ++l) av[l] = st[(l * W + o1) * kSlot + at];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+          if (NR > 1 && j >= nrhs) break;
+          const float2 xv = in ? xm[(long long)j * ndof + j1] : make_float2(0.0f, 0.0f);
+#pragma unroll
+          for (int l = 0; l < DIM; ++l) df_madd(sh[j][l], sl[j][l], av[l], xv);
+        }
       }
 #pragma unroll
-      for (int l = 0; l < DIM; ++l) {   // renormalise (Fast2Sum) after each neighbour row
-        const float t = __fadd_rn(sh[l], sl[l]);
-        sl[l] = __fsub_rn(sl[l], __fsub_rn(t, sh[l]));
-        sh[l] = t;
-      }
+      for (int j = 0; j < NR; ++j)
+#pragma unroll
+        for (int l = 0; l < DIM; ++l) {   // renormalise (Fast2Sum) after each neighbour row
+          const float t = __fadd_rn(sh[j][l], sl[j][l]);
+          sl[j][l] = __fsub_rn(sl[j][l], __fsub_rn(t, sh[j][l]));
+          sh[j][l] = t;
+        }
     }
     __syncwarp();
     if (lane == 0)
@@ -347,7 +373,12 @@ __global__ void __launch_bounds__(kRowsTN + 32) k_stencil_mv_rows(const DevPatch
   if (act) {
     const int node = i1 + n1 * rr;
 #pragma unroll
-    for (int l = 0; l < DIM; ++l) y[pt.off + (long long)l * N + node] = (double)sh[l] + (double)sl[l];
+    for (int j = 0; j < NR; ++j) {
+      if (NR > 1 && j >= nrhs) break;
+#pragma unroll
+      for (int l = 0; l < DIM; ++l)
+        y[(long long)j * ystride + pt.off + (long long)l * N + node] = (double)sh[j][l] + (double)sl[j][l];
+    }
   }
 }
 
@@ -359,45 +390,62 @@ static int uniform_degree(const afi_ctx *c) {
   return pu;
 }
 
+// nr right-hand sides x_j = x + j xstride, y_j = y + j ystride (nr = 1:
+// the single-vector kernel; 2..kMaxRhs: the batched one)
 template <int DIM, int PC>
-static afi_status rows_launch(afi_ctx *c, const double *x, double *y, cudaStream_t s, bool set_attr) {
+static afi_status rows_launch(afi_ctx *c, const double *x, long long xstride, double *y,
+                              long long ystride, int nr, cudaStream_t s, bool set_attr) {
   using C = RowsCfg<DIM, PC>;
-  auto kern = k_stencil_mv_rows<DIM, PC>;
+  auto kern1 = k_stencil_mv_rows<DIM, PC, 1>;
+  auto kern2 = k_stencil_mv_rows<DIM, PC, 2>;
+  auto kern4 = k_stencil_mv_rows<DIM, PC, 4>;
+  auto kern8 = k_stencil_mv_rows<DIM, PC, 8>;
   if (set_attr) {
-    AFI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    AFI_CUDA(cudaFuncSetAttribute(kern1, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    AFI_CUDA(cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    AFI_CUDA(cudaFuncSetAttribute(kern4, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    AFI_CUDA(cudaFuncSetAttribute(kern8, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
     return AFI_OK;
   }
+  auto kernm = nr <= 2 ? kern2 : (nr <= 4 ? kern4 : kern8);
   int tiles = 0;
   for (auto &p : c->hp) {
     const int R = kRowsTN / p.n[0], rows = p.n[1] * p.n[2];
     tiles = std::max(tiles, (rows + R - 1) / R);
   }
-  launch(k_split_x, (unsigned)((c->n_dof + 255) / 256), 256, 0, s, x, c->xsplit, c->n_dof,
-         (const double *)c->gate);
-  launch(kern, dim3(tiles, c->npatch), kRowsTN + 32, C::SMEM, s, (const DevPatch *)c->patches,
-         (const float2 *)c->stencil2, (const float2 *)c->xsplit, y, (const double *)c->gate, c->dflag + 1);
+  float2 *xs = nr > 1 ? c->xsplit_multi : c->xsplit;
+  launch(k_split_x_multi, dim3((unsigned)((c->n_dof + 255) / 256), nr), 256, 0, s, x, xstride, xs,
+         c->n_dof, (const double *)c->gate);
+  if (nr == 1)
+    launch(kern1, dim3(tiles, c->npatch), kRowsTN + 32, C::SMEM, s, (const DevPatch *)c->patches,
+           (const float2 *)c->stencil2, (const float2 *)xs, y, (const double *)c->gate, c->dflag + 1,
+           1, c->n_dof, ystride);
+  else
+    launch(kernm, dim3(tiles, c->npatch), kRowsTN + 32, C::SMEM, s, (const DevPatch *)c->patches,
+           (const float2 *)c->stencil2, (const float2 *)xs, y, (const double *)c->gate, c->dflag + 1,
+           nr, c->n_dof, ystride);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
 
 // the instantiation for (dim, uniform degree); false if there is none
-static bool rows_dispatch(afi_ctx *c, const double *x, double *y, cudaStream_t s, bool set_attr,
-                          afi_status *st) {
+static bool rows_dispatch(afi_ctx *c, const double *x, long long xstride, double *y,
+                          long long ystride, int nr, cudaStream_t s, bool set_attr, afi_status *st) {
   const int pu = uniform_degree(c);
   if (c->dim == 3) {
     switch (pu) {
-      case 1: *st = rows_launch<3, 1>(c, x, y, s, set_attr); return true;
-      case 2: *st = rows_launch<3, 2>(c, x, y, s, set_attr); return true;
-      case 3: *st = rows_launch<3, 3>(c, x, y, s, set_attr); return true;
-      case 4: *st = rows_launch<3, 4>(c, x, y, s, set_attr); return true;
-      case 5: *st = rows_launch<3, 5>(c, x, y, s, set_attr); return true;
+      case 1: *st = rows_launch<3, 1>(c, x, xstride, y, ystride, nr, s, set_attr); return true;
+      case 2: *st = rows_launch<3, 2>(c, x, xstride, y, ystride, nr, s, set_attr); return true;
+      case 3: *st = rows_launch<3, 3>(c, x, xstride, y, ystride, nr, s, set_attr); return true;
+      case 4: *st = rows_launch<3, 4>(c, x, xstride, y, ystride, nr, s, set_attr); return true;
+      case 5: *st = rows_launch<3, 5>(c, x, xstride, y, ystride, nr, s, set_attr); return true;
       default: return false;
     }
   }
   switch (pu) {
-    case 1: *st = rows_launch<2, 1>(c, x, y, s, set_attr); return true;
-    case 2: *st = rows_launch<2, 2>(c, x, y, s, set_attr); return true;
-    case 3: *st = rows_launch<2, 3>(c, x, y, s, set_attr); return true;
+    case 1: *st = rows_launch<2, 1>(c, x, xstride, y, ystride, nr, s, set_attr); return true;
+    case 2: *st = rows_launch<2, 2>(c, x, xstride, y, ystride, nr, s, set_attr); return true;
+    case 3: *st = rows_launch<2, 3>(c, x, xstride, y, ystride, nr, s, set_attr); return true;
     default: return false;
   }
 }
@@ -444,7 +492,7 @@ afi_status stencil_to_pairs(afi_ctx *c) {
   else launch(k_stencil_pack<2>, g, 256, 0, 0, (const DevPatch *)c->patches, (const double *)c->stencil, c->stencil2);
   AFI_LAUNCH_CHECK();
   afi_status st = AFI_OK;
-  rows_dispatch(c, nullptr, nullptr, 0, true, &st);
+  rows_dispatch(c, nullptr, 0, nullptr, 0, 1, 0, true, &st);
   return st;
 }
 
@@ -458,10 +506,93 @@ afi_status op_stiffness_fp64(afi_ctx *c, const double *x, double *y, cudaStream_
   return st;
 }
 
+// y_j = A x_j for nr <= kMaxRhs vectors at the given strides: one launch of
+// the batched double-FP32 kernel when the pair copy exists (the coefficients
+// stream once for all of them), else one FP64 launch per vector.
+static afi_status multi_launches(afi_ctx *c, const double *x, long long xstride, double *y,
+                                 long long ystride, int nr, int width, cudaStream_t s) {
+  for (int j = 0; j < nr; j += width) {
+    afi_status st = AFI_OK;
+    if (!rows_dispatch(c, x + j * xstride, xstride, y + j * ystride, ystride,
+                       std::min(width, nr - j), s, false, &st)) {
+      set_error("op_stiffness_multi: no batched kernel for this degree");
+      return AFI_EINVAL;
+    }
+    AFI_TRY(st);
+  }
+  return AFI_OK;
+}
+
+// The number of vectors per launch of the batched kernel, chosen once per
+// context by timing 8 vectors in launches of 1, 2, 4 and 8 (best of three
+// after a warm-up) on scratch data: more vectors per launch share each
+// coefficient but hold more accumulators per thread (fewer resident CTAs).
+static afi_status tune_multi_width(afi_ctx *c, cudaStream_t s) {
+  if (c->mv_width > 0) return AFI_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  AFI_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) { c->mv_width = kMaxRhs; return AFI_OK; }
+  double *buf = nullptr;
+  AFI_TRY(dalloc(c, (void **)&buf, (size_t)2 * kMaxRhs * c->n_dof * sizeof(double)));
+  AFI_CUDA(cudaMemsetAsync(buf, 0, (size_t)2 * kMaxRhs * c->n_dof * sizeof(double), s));
+  cudaEvent_t e0, e1;
+  AFI_CUDA(cudaEventCreate(&e0));
+  AFI_CUDA(cudaEventCreate(&e1));
+  const double *gate = c->gate;
+  c->gate = nullptr;
+  afi_status st = AFI_OK;
+  float best = 1e30f;
+  int bw = kMaxRhs;
+  for (int w : {1, 2, 4, 8}) {
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4 && st == AFI_OK; ++rep) {
+      cudaEventRecord(e0, s);
+      st = multi_launches(c, buf, c->n_dof, buf + (long long)kMaxRhs * c->n_dof, c->n_dof,
+                          kMaxRhs, w, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    if (tmin < best) { best = tmin; bw = w; }
+  }
+  c->gate = gate;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  c->bytes -= (long long)2 * kMaxRhs * c->n_dof * sizeof(double);
+  AFI_TRY(st);
+  c->mv_width = bw;
+  return AFI_OK;
+}
+
+// Buffers and launch width of the batched stiffness, set up before any
+// stream capture.
+afi_status stiffness_multi_prepare(afi_ctx *c, cudaStream_t s) {
+  if (!c->stencil2 || uniform_degree(c) == 0) return AFI_OK;
+  if (!c->xsplit_multi)
+    AFI_TRY(dalloc(c, (void **)&c->xsplit_multi, (size_t)kMaxRhs * c->n_dof * sizeof(float2)));
+  return tune_multi_width(c, s);
+}
+
+afi_status op_stiffness_multi(afi_ctx *c, const double *x, long long xstride, double *y,
+                              long long ystride, int nr, cudaStream_t s) {
+  if (nr < 1 || nr > kMaxRhs) { set_error("op_stiffness_multi: bad batch"); return AFI_EINVAL; }
+  if (c->stencil2 && !c->mv_exact && nr > 1 && uniform_degree(c) > 0) {
+    if (!c->xsplit_multi)
+      AFI_TRY(dalloc(c, (void **)&c->xsplit_multi, (size_t)kMaxRhs * c->n_dof * sizeof(float2)));
+    AFI_TRY(tune_multi_width(c, s));
+    return multi_launches(c, x, xstride, y, ystride, nr, c->mv_width, s);
+  }
+  for (int j = 0; j < nr; ++j) AFI_TRY(op_stiffness(c, x + j * xstride, y + j * ystride, s));
+  return AFI_OK;
+}
+
 afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->stencil2 && !c->mv_exact) {
     afi_status st = AFI_OK;
-    if (rows_dispatch(c, x, y, s, false, &st)) return st;
+    if (rows_dispatch(c, x, 0, y, 0, 1, s, false, &st)) return st;
   }
   dim3 g((c->max_N + 127) / 128, c->npatch);
   const int pu = uniform_degree(c);   // one degree for every patch -> specialised kernel
