@@ -107,13 +107,17 @@ __device__ __forceinline__ Dims dims_of(const DevPatch &pt, int interior) {
 // Algorithm 1 on the tensor in `cur` (ping-pong with `oth`).  Returns the
 // buffer that holds the result.
 template <typename T>
-__device__ T *fd_tensor(T *cur, T *oth, const DevPatch &pt, const Tab1D *tabs, const T *tpool,
-                        int dim, int l, int interior) {
+__device__ T *fd_tensor(T *cur, T *oth, const DevPatch &pt, const DevPatch *pglob,
+                        const Tab1D *tabs, const T *tpool, int dim, int l, int interior) {
   const Dims D = dims_of(pt, interior);
   const T *Uf[3], *Ub[3], *Dv[3];
   int ld[3];
+  // component-indexed fields straight from global memory (pt is a local
+  // copy, which a runtime index would move to local memory)
+  const DevPatch &pg = *pglob;
+  const int lt[3] = {pg.ltab[l][0], pg.ltab[l][1], pg.ltab[l][2]};
   for (int d = 0; d < 3; ++d) {
-    const Tab1D tb = tabs[pt.ltab[l][d]];
+    const Tab1D tb = tabs[lt[d]];
     Uf[d] = tpool + (interior ? tb.Uip : tb.Up);
     Ub[d] = tpool + (interior ? tb.Uipt : tb.Upt);
     Dv[d] = tpool + (interior ? tb.Di : tb.D);
@@ -125,7 +129,7 @@ __device__ T *fd_tensor(T *cur, T *oth, const DevPatch &pt, const Tab1D *tabs, c
     T *t = cur; cur = oth; oth = t;
   }
   const T hs = (T)pt.lscale, sh = (T)pt.lshift;
-  const T c0 = (T)pt.lcf[l][0], c1 = (T)pt.lcf[l][1], c2 = (T)pt.lcf[l][2];
+  const T c0 = (T)pg.lcf[l][0], c1 = (T)pg.lcf[l][1], c2 = (T)pg.lcf[l][2];
   for (int idx = threadIdx.x; idx < D.N; idx += blockDim.x) {   // q~ = Lambda^{-1} r~
     const int i1 = idx % D.n[0], i2 = (idx / D.n[0]) % D.n[1], i3 = idx / (D.n[0] * D.n[1]);
     T lam = c0 * Dv[0][i1] + c1 * Dv[1][i2] + (dim == 3 ? c2 * Dv[2][i3] : T(0));
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(512) k_fd(const DevPatch *P, const Tab1D *tabs
   T *b1 = b0 + D.N;
   load_block<T>(r + base, b0, D.N);
   __syncthreads();
-  const T *res = fd_tensor<T>(b0, b1, pt, tabs, tpool, dim, l, interior);
+  const T *res = fd_tensor<T>(b0, b1, pt, P + k, tabs, tpool, dim, l, interior);
   for (int i = threadIdx.x; i < D.N; i += blockDim.x) s[base + i] = to_f64(res[i]);
 }
 

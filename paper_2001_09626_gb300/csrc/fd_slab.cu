@@ -144,13 +144,16 @@ __global__ void __launch_bounds__(256, 4) k_fd_plane(const DevPatch *P, const Ta
   }
   __syncthreads();
   // both products use one B slot when directions 1 and 2 share a table
-  const int slot1 = (pt.ltab[l][0] == pt.ltab[l][1]) ? 0 : 1;
+  // this component's tables, read from global memory (not from the local
+  // copy, which a runtime index would move to local memory)
+  const int lt0 = P[w.x].ltab[l][0], lt1 = P[w.x].ltab[l][1];
+  const int slot1 = (lt0 == lt1) ? 0 : 1;
   if (tid == 0) {
     const uint32_t b0 = (uint32_t)(rup(n1, 16) * rup(n1, KSTEP) * (int)sizeof(T));
     const uint32_t b1 = (uint32_t)(rup(n2, 16) * rup(n2, KSTEP) * (int)sizeof(T));
     expect_tx(&tma_bar, slot1 ? b0 + b1 : b0);
-    bulk_g2s(bm, tcpool + tabs[pt.ltab[l][0]].tcB[FMT == 1][interior][BACK], b0, &tma_bar);
-    if (slot1) bulk_g2s(bm + bsz, tcpool + tabs[pt.ltab[l][1]].tcB[FMT == 1][interior][BACK], b1, &tma_bar);
+    bulk_g2s(bm, tcpool + tabs[lt0].tcB[FMT == 1][interior][BACK], b0, &tma_bar);
+    if (slot1) bulk_g2s(bm + bsz, tcpool + tabs[lt1].tcB[FMT == 1][interior][BACK], b1, &tma_bar);
   }
   {
     uint4 *zp = reinterpret_cast<uint4 *>(A);
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
   __syncthreads();
   const uint32_t bbytes = (uint32_t)(rup(n3, 16) * rup(n3, KSTEP) * (int)sizeof(T));
   if (tid == 0) {
-    const Tab1D &tb = tabs[pt.ltab[l][2]];
+    const Tab1D &tb = tabs[P[w.x].ltab[l][2]];
     stage_b(&tma_bar, bm, bsz, tcpool, tb.tcB[FMT == 1][interior][0], bbytes,
             tb.tcB[FMT == 1][interior][1], bbytes);
   }
@@ -430,10 +433,12 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
   const int row = q * 32 + lane;
   // Lambda = c1 D1[a1] + c2 D2[a2] + c3 D3[a3] (+1, times H^{d-2}, for P_A)
   const float hs = (float)pt.lscale, shf = (float)pt.lshift;
-  const float c0 = (float)pt.lcf[l][0], c1 = (float)pt.lcf[l][1], c2 = (float)pt.lcf[l][2];
-  const float *D0 = fpool + (interior ? tabs[pt.ltab[l][0]].Di : tabs[pt.ltab[l][0]].D);
-  const float *D1 = fpool + (interior ? tabs[pt.ltab[l][1]].Di : tabs[pt.ltab[l][1]].D);
-  const float *D2 = fpool + (interior ? tabs[pt.ltab[l][2]].Di : tabs[pt.ltab[l][2]].D);
+  const DevPatch &pg = P[w.x];   // component-indexed fields straight from global memory
+  const float c0 = (float)pg.lcf[l][0], c1 = (float)pg.lcf[l][1], c2 = (float)pg.lcf[l][2];
+  const int t0 = pg.ltab[l][0], t1 = pg.ltab[l][1], t2 = pg.ltab[l][2];
+  const float *D0 = fpool + (interior ? tabs[t0].Di : tabs[t0].D);
+  const float *D1 = fpool + (interior ? tabs[t1].Di : tabs[t1].D);
+  const float *D2 = fpool + (interior ? tabs[t2].Di : tabs[t2].D);
   float lab = 0.f;
   if (row < nl) {
     const int line = line0 + row, a2 = line / n1, a1 = line - a2 * n1;

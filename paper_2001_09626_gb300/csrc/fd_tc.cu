@@ -80,7 +80,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
   const int N = n[0] * n[1] * n[2];
   const long long base =
       (interior ? pt.ioff : pt.off) + (long long)l * N + (long long)blockIdx.z * rhs_stride;
-  const unsigned bs = b_slots(pt.ltab[l][0], pt.ltab[l][1], pt.ltab[l][2]);
+  // this component's tables and coefficients, read from global memory
+  // (indexing the local copy by the runtime component would move it to
+  // local memory)
+  const int lt0 = P[k].ltab[l][0], lt1 = P[k].ltab[l][1], lt2 = P[k].ltab[l][2];
+  const unsigned bs = b_slots(lt0, lt1, lt2);
 
   // stage the B operands (prebuilt in the canonical layout) with TMA bulk
   // copies while the threads zero the operand buffer
@@ -107,7 +111,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
     for (int m = 0; m < 6; ++m) {
       if (!(first & (1u << m))) continue;
       const int nd = n[m % 3];
-      const long long off = tabs[pt.ltab[l][m % 3]].tcB[FMT == 1][interior][m >= 3];
+      const int tm = (m % 3 == 0) ? lt0 : (m % 3 == 1 ? lt1 : lt2);
+      const long long off = tabs[tm].tcB[FMT == 1][interior][m >= 3];
       bulk_g2s(bm + bslot(bs, m) * bsz, tcpool + off,
                (uint32_t)(rup(nd, 16) * rup(nd, KSTEP) * (int)sizeof(T)), &tma_bar);
     }
@@ -160,10 +165,10 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
 
   // Lambda for this (patch, component)
   const float hs = (float)pt.lscale, shf = (float)pt.lshift;
-  const float c0 = (float)pt.lcf[l][0], c1 = (float)pt.lcf[l][1], c2 = (float)pt.lcf[l][2];
+  const float c0 = (float)P[k].lcf[l][0], c1 = (float)P[k].lcf[l][1], c2 = (float)P[k].lcf[l][2];
   const float *Dv[3];
   for (int d = 0; d < 3; ++d) {
-    const Tab1D tb = tabs[pt.ltab[l][d]];
+    const Tab1D tb = tabs[d == 0 ? lt0 : (d == 1 ? lt1 : lt2)];
     Dv[d] = fpool + (interior ? tb.Di : tb.D);
   }
 
