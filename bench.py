@@ -17,6 +17,12 @@ INEXACT timings, the reported solve time includes the local-solver setup
 (Algorithm 1 step 1, timed once by the library and added to the measured
 solve); the stiffness assembly and constraint setup are reported as setup_s.
 
+Beside the headline the line reports the plain FP64 form, the mixed form
+with the FP64 stencil, eight right-hand sides solved together (multi_rhs),
+the geometry-inclusion local solvers of Section 5.2.3 on the same problem
+(geometry_inclusion), FD-apply rates and the rooflines of the dominant
+kernels.
+
   python bench.py [--gpus N --steps K --warmup W --prec fp32|fp64|tf32|bf16]
   python bench.py --impl reference ...   (the CPU oracle as the reference arm)
 
@@ -434,6 +440,44 @@ def run_ours(args):
     s64.close()
     fp64_peak = fp64_peak_tflops()
 
+    # eight seeded right-hand sides solved together (lockstep MINRES, one
+    # batched stiffness launch per iteration) against one at a time
+    F8 = torch.stack([s.load_vector(W.body_force_coeffs(prob, seed=100 + j)) for j in range(8)])
+    s.solve(F8)
+    ms_multi = timed(lambda: s.solve(F8), 1)
+    info_multi = dict(s.last_info)
+    X8 = torch.rand(8, s.n_dof, dtype=torch.float64, device="cuda")
+    Y8 = torch.empty_like(X8)
+    for _ in range(2):
+        A.afi_apply_batch(s.ctx, A.AFI_OP_STIFFNESS, X8, Y8, 8)
+    mv8_ms = timed(lambda: A.afi_apply_batch(s.ctx, A.AFI_OP_STIFFNESS, X8, Y8, 8), 5)
+    multi_rhs = {"nrhs": 8, "solve_s": round((ms_multi + fd_setup_ms) / 1e3, 4),
+                 "per_rhs_s": round((ms_multi / 8 + fd_setup_ms) / 1e3, 4),
+                 "iterations_max": info_multi["iters"], "relres_true_max": info_multi["relres_true"],
+                 "one_at_a_time_s": round(8 * ms_solve / 1e3, 4),
+                 "speedup_vs_one_at_a_time": round(8 * ms_solve / ms_multi, 3),
+                 "stiffness_8_vectors_ms": round(mv8_ms, 3),
+                 "stiffness_1_vector_ms": None}
+
+    # the paper's geometry-inclusion local solvers (Section 5.2.3) on the
+    # same problem and right-hand side: fit, tables and scalings are
+    # local-solver setup and are counted in the solve time
+    try:
+        t0g = time.time()
+        sg = Solver(prob, prec=args.prec, tol=1e-8, maxit=5000, use_graph=True, geo=True)
+        torch.cuda.synchronize()
+        setup_geo = time.time() - t0g
+        sg.solve(f)
+        ms_geo = timed(lambda: sg.solve(f), max(1, min(args.steps, 3)))
+        info_geo = dict(sg.last_info)
+        sg.close()
+        geometry_inclusion = {"solve_s": round((ms_geo + info_geo["t_fd_setup_ms"]) / 1e3, 4),
+                              "iterations": info_geo["iters"], "relres_true": info_geo["relres_true"],
+                              "fit_and_tables_s": round(info_geo["t_fd_setup_ms"] / 1e3, 4),
+                              "setup_s": round(setup_geo, 3)}
+    except A.AfiError as e:   # a second context of a large workload may not fit
+        geometry_inclusion = {"skipped": str(e)}
+
     # FD apply throughput (P_A^{-1} on every patch and component), one
     # right-hand side and a batch of 8 in one launch
     r = torch.rand(s.n_dof, dtype=torch.float64, device="cuda")
@@ -453,6 +497,7 @@ def run_ours(args):
     for _ in range(3):
         s.apply(A.AFI_OP_STIFFNESS, x)
     mv_ms = timed(lambda: s.apply(A.AFI_OP_STIFFNESS, x), 20)
+    multi_rhs["stiffness_1_vector_ms"] = round(mv_ms, 4)
     flops, stored_bytes = stencil_stats(prob)
     peaks = {}
     try:
@@ -513,6 +558,7 @@ def run_ours(args):
             "mixed_fp64_stencil": {"solve_s": round((ms_mixed64 + info_mixed64["t_fd_setup_ms"]) / 1e3, 4),
                                    "iterations": info_mixed64["iters"],
                                    "relres_true": info_mixed64["relres_true"]},
+            "multi_rhs": multi_rhs, "geometry_inclusion": geometry_inclusion,
             "fd_apply_dofs_per_s": {k: round(s.n_dof / (v * 1e-3), 1) for k, v in fd_ms.items()},
             "fd_apply_dofs_per_s_nrhs8": {k: round(8 * s.n_dof / (v * 1e-3), 1)
                                           for k, v in fd8_ms.items()},
