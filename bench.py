@@ -534,7 +534,9 @@ def run_ours(args):
                    "bytes_per_launch": fd_bytes,
                    "nrhs8": {"achieved": round(8 * fd_bytes / (fd8_ms[args.prec] * 1e-3) / 1e9, 1),
                              "frac": round(8 * fd_bytes / (fd8_ms[args.prec] * 1e-3) / 1e9 / hbm, 4),
-                             "launch_ms": round(fd8_ms[args.prec], 4)}}
+                             "launch_ms": round(fd8_ms[args.prec], 4),
+                             "traffic": (traffic_record("k_fd_tc_nrhs8")
+                                         if args.workload == "C2" and args.prec == "tf32" else None)}}
 
     line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
