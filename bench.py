@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--fd-slab", action="store_true",
                     help="--fd-only: send every tensor through the three-pass kernels")
     ap.add_argument("--precs", default="fp64,fp32,tf32,bf16", help="--fd-only: precisions to time")
+    ap.add_argument("--fd-fixed", action="store_true",
+                    help="--fd-only: the fixed FD work split instead of the timed one")
     return ap.parse_args()
 
 
@@ -595,7 +597,8 @@ def run_fd_only(args):
     import afi_workloads as W
     from paper_2001_09626_gb300.solver import Solver
     prob = W.config(args.workload)
-    s = Solver(prob, prec=args.prec, tol=1e-8, local_only=True, fd_slab=args.fd_slab)
+    s = Solver(prob, prec=args.prec, tol=1e-8, local_only=True, fd_slab=args.fd_slab,
+               fd_fixed=args.fd_fixed)
     stream = torch.cuda.current_stream()
     peaks = {}
     try:
@@ -639,7 +642,8 @@ def run_fd_only(args):
                     "frac_hbm": round(16 * dofs / (ms * 1e-3) / 1e9 / hbm, 4)}
         out[prec] = row
     line = {"metric": "FD-apply DoF/s", "unit": "DoF/s", "workload": args.workload,
-            "path": "three-pass (forced)" if args.fd_slab else "automatic",
+            "path": ("three-pass (forced)" if args.fd_slab else
+                     ("fixed split" if args.fd_fixed else "timed split")),
             "n_dof": s.n_dof, "n_int": n_int, "hbm_peak_GBs": hbm, "fd": out}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_fd_rate(args.workload)

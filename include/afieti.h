@@ -159,6 +159,19 @@ typedef struct {
                                       AFI_EINVAL.  The fit and the per-(patch,
                                       component) tables count as local-solver
                                       setup (afi_info.t_fd_setup_ms). */
+#define AFI_VARIANT_FD_FIXED 64    /* TF32/BF16 local solvers on 3D tensors of
+                                      several shapes: keep every tensor that
+                                      fits one CTA in the single-CTA kernel.
+                                      By default the split between it and the
+                                      three-pass kernels is chosen at setup by
+                                      timing one application per candidate
+                                      (each distinct shared-memory need of the
+                                      tensors is a candidate threshold), so two
+                                      contexts of one problem may split
+                                      differently and round differently; this
+                                      bit makes the split a fixed rule.  A
+                                      batch of tensors of one shape has a
+                                      single candidate and is never timed. */
 
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
  * preconditioned residual estimate and then the true FP64 residual

@@ -170,6 +170,7 @@ AFI_VARIANT_STENCIL_F64 = 4
 AFI_VARIANT_FORCE_RESTART = 8
 AFI_VARIANT_EXACT = 16
 AFI_VARIANT_GEO = 32
+AFI_VARIANT_FD_FIXED = 64
 
 
 def af_ieti_setup(prob, prec="fp64", tol=1e-8, maxit=2000, use_graph=False, variant=0):

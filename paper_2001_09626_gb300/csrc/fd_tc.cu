@@ -289,14 +289,18 @@ static size_t tc_smem(int cap, int bsz, int tcols, int nslot, int fmt) {
   return std::max(smem, floor_smem);
 }
 
-// Patches in increasing order of need join the tensor-core list while the
-// combined launch still fits; the rest go to the SIMT kernel.
-static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
+// Patches in increasing order of need join the single-CTA tensor-core list
+// while the combined launch still fits and their own need is at most thr;
+// the rest go to the three-pass kernels, else to the SIMT kernel.  One launch
+// gives every CTA the shared memory of the largest tensor in the list, so a
+// low thr keeps the small tensors' residency high.
+static afi_status build_split_thr(afi_ctx *c, int interior, int fmt, size_t thr, TcSplit &sp) {
   std::vector<std::pair<size_t, int>> order;
   const bool force_slab = (c->opt.variant & AFI_VARIANT_FD_SLAB) != 0;
   for (int k = 0; k < c->npatch; ++k) {
     const TcNeed t = tc_need(c->hp[k], interior, fmt);
-    if (t.ok && !force_slab) order.push_back({tc_smem(t.cap, t.bsz, t.tcols, t.nslot, fmt), k});
+    const size_t need = tc_smem(t.cap, t.bsz, t.tcols, t.nslot, fmt);
+    if (t.ok && !force_slab && need <= thr) order.push_back({need, k});
   }
   std::sort(order.begin(), order.end());
   std::vector<int> tc, simt;
@@ -338,6 +342,74 @@ static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
   return AFI_OK;
 }
 
+static void free_split(TcSplit &sp) {
+  void *p[] = {sp.d_tc, sp.d_simt, sp.d_plane, sp.d_line};
+  for (void *q : p)
+    if (q) cudaFree(q);
+  sp = TcSplit{};
+}
+
+static afi_status run_split(afi_ctx *c, int interior, int fmt, const TcSplit &sp, const double *r,
+                            double *s, cudaStream_t st, int nrhs);
+
+// Project-written autotuner of the FD work split, per (interior, operand
+// format): every distinct shared-memory need of the tensors that fit one CTA
+// is a candidate threshold (tensors above it take the three-pass kernels);
+// each candidate's split is timed on one application (best of three after
+// a warm-up) and the fastest kept.  A single candidate (tensors of one
+// shape) needs no timing.  AFI_VARIANT_FD_FIXED keeps every tensor that fits
+// one CTA in the single-CTA kernel instead.
+static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
+  const size_t all = (size_t)-1;
+  std::vector<size_t> cand;
+  for (int k = 0; k < c->npatch; ++k) {
+    const TcNeed t = tc_need(c->hp[k], interior, fmt);
+    const size_t need = tc_smem(t.cap, t.bsz, t.tcols, t.nslot, fmt);
+    if (t.ok && need <= (size_t)g_tc_dyn_max) cand.push_back(need);
+  }
+  std::sort(cand.begin(), cand.end());
+  cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+  const bool fixed = (c->opt.variant & (AFI_VARIANT_FD_FIXED | AFI_VARIANT_FD_SLAB)) != 0 ||
+                     c->dim != 3;
+  if (fixed || cand.size() <= 1) return build_split_thr(c, interior, fmt, all, sp);
+  cand.insert(cand.begin(), 0);   // every 3D tensor through the three-pass kernels
+  const long long n = interior ? c->n_int : c->n_dof;
+  double *buf = nullptr;
+  AFI_CUDA(cudaMalloc(&buf, (size_t)2 * n * sizeof(double)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemset(buf, 0, (size_t)2 * n * sizeof(double));
+  const double *gate = c->gate;
+  c->gate = nullptr;
+  afi_status st = AFI_OK;
+  float best = 1e30f;
+  size_t bthr = all;
+  for (size_t thr : cand) {
+    TcSplit tmp;
+    st = build_split_thr(c, interior, fmt, thr, tmp);
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 4 && st == AFI_OK; ++rep) {
+      cudaEventRecord(e0, 0);
+      st = run_split(c, interior, fmt, tmp, buf, buf + n, 0, 1);
+      cudaEventRecord(e1, 0);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tmin = std::min(tmin, ms);
+    }
+    free_split(tmp);
+    if (st != AFI_OK) break;
+    if (tmin < best) { best = tmin; bthr = thr; }
+  }
+  c->gate = gate;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(buf);
+  AFI_TRY(st);
+  return build_split_thr(c, interior, fmt, bthr, sp);
+}
+
 afi_status fd_tc_prepare(afi_ctx *c) {
   const void *fns[] = {(const void *)k_fd_tc<2, 256>, (const void *)k_fd_tc<2, 512>,
                        (const void *)k_fd_tc<1, 256>, (const void *)k_fd_tc<1, 512>};
@@ -361,6 +433,11 @@ afi_status fd_tc_run(afi_ctx *c, int interior, const double *r, double *s, cudaS
   const int fmt = (c->opt.prec == AFI_FD_BF16) ? 1 : 2;
   TcSplit &sp = c->tcsplit[interior][fmt == 1];
   if (!sp.ready) AFI_TRY(build_split(c, interior, fmt, sp));
+  return run_split(c, interior, fmt, sp, r, s, st, nrhs);
+}
+
+static afi_status run_split(afi_ctx *c, int interior, int fmt, const TcSplit &sp, const double *r,
+                            double *s, cudaStream_t st, int nrhs) {
   const long long stride = interior ? c->n_int : c->n_dof;
   if (sp.ntc) {
     const dim3 grid(sp.ntc, c->dim, nrhs);
