@@ -61,41 +61,22 @@ __device__ __forceinline__ void stage_b(uint64_t *bar, T *bm, int bsz, const uns
 __device__ __forceinline__ void ld4(const double *p, float *v) {
   const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
   const double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
-  v[0] = f64_to_f32(a.x); v[1] = f64_to_f32(a.y); v[2] = f64_to_f32(b.x); v[3] = f64_to_f32(b.y);
+  v[0] = f64_to_op(a.x); v[1] = f64_to_op(a.y); v[2] = f64_to_op(b.x); v[3] = f64_to_op(b.y);
 }
 __device__ __forceinline__ void ld4(const float *p, float *v) {
   const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
   v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
 }
-// four consecutive K entries of one operand row (16-byte / 8-byte aligned)
-template <int FMT> __device__ __forceinline__ void st4(typename Op<FMT>::T *p, const float *v);
-template <> __device__ __forceinline__ void st4<2>(float *p, const float *v) {
-  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-template <> __device__ __forceinline__ void st4<1>(__nv_bfloat16 *p, const float *v) {
-  __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v[0], v[1]), __floats2bfloat162_rn(v[2], v[3])};
-  *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(h);
-}
-
 // two consecutive inputs (aligned to their pair size) as FP32
 __device__ __forceinline__ void ld2(const double *p, float *v) {
   const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
-  v[0] = f64_to_f32(a.x); v[1] = f64_to_f32(a.y);
+  v[0] = f64_to_op(a.x); v[1] = f64_to_op(a.y);
 }
 __device__ __forceinline__ void ld2(const float *p, float *v) {
   const float2 a = __ldg(reinterpret_cast<const float2 *>(p));
   v[0] = a.x; v[1] = a.y;
 }
-// two consecutive K entries of one operand row (8-byte / 4-byte aligned)
-template <int FMT> __device__ __forceinline__ void st2(typename Op<FMT>::T *p, const float *v);
-template <> __device__ __forceinline__ void st2<2>(float *p, const float *v) {
-  *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-}
-template <> __device__ __forceinline__ void st2<1>(__nv_bfloat16 *p, const float *v) {
-  *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v[0], v[1]);
-}
-
-__device__ __forceinline__ float ld_in(const double *p) { return f64_to_f32(__ldg(p)); }
+__device__ __forceinline__ float ld_in(const double *p) { return f64_to_op(__ldg(p)); }
 __device__ __forceinline__ float ld_in(const float *p) { return __ldg(p); }
 __device__ __forceinline__ void st_out(double *p, float v) { *p = f32_to_f64(v); }
 __device__ __forceinline__ void st_out(float *p, float v) { *p = v; }

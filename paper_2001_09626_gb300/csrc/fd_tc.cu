@@ -15,12 +15,17 @@
 // to global memory.
 //
 // Operands use the no-swizzle K-major layout of core matrices (8 rows x 16
-// bytes); one elected thread issues the MMAs (M = 128 lines per tile, N =
-// output modes padded to 16, K in steps of 32 bytes) and commits them to an
-// mbarrier that all threads wait on with a bounded spin.  The tensor operand
+// bytes).  The tensor operand stores each 16-byte K chunk of all its rows as
+// one slab, rows 16 bytes apart (stride between 8-row groups 128 bytes) and
+// chunks (Lp + 1) x 16 bytes apart (Lp = lines padded to the 128-line
+// tile), so an element's offset is linear in its row and a warp writing one
+// row across its K chunks touches distinct banks.  One elected thread issues
+// the MMAs (M = 128 lines per tile, N = output modes padded to 16, K in steps
+// of 32 bytes), commits them to an mbarrier and waits on it with a bounded
+// spin while the other threads wait at the CTA barrier.  The tensor operand
 // lives in a single shared-memory buffer that each epilogue overwrites in
 // place, so three to four CTAs share an SM; FP64 <-> FP32 conversions of the
-// input and output run on the integer pipes (f64_to_f32 / f32_to_f64).
+// input and output run on the integer pipes (f64_to_op / f32_to_f64).
 #include "tc.cuh"
 
 #include <algorithm>
@@ -50,6 +55,66 @@ __host__ __device__ __forceinline__ int bslot(unsigned packed, int m) {
   return (int)((packed >> (4 * m)) & 15u);
 }
 
+// element offset of (row, k) in the tensor operand: K chunk k / T16 of
+// lbo = (Lp + 1) T16 elements, rows T16 elements apart
+template <int FMT>
+__device__ __forceinline__ int kslab(int row, int k, int lbo) {
+  constexpr int T16 = tc::Op<FMT>::T16;
+  return (k / T16) * lbo + row * T16 + (k % T16);
+}
+
+// Epilogue of one mode product: D[line][j] from tensor memory to registers,
+// then (KIND 0) into the next operand with the axes rotated, in place;
+// (KIND 1) the same after the scaling by Lambda^{-1}; (KIND 2) as FP64 into
+// the output.  Work items are (128-line tile, 8 columns), split between the
+// NT / 128 warps that share a tensor-memory lane quarter.  The current operand is [c][b][a] (a = na fastest); line =
+// b + nb c, j = a; the next operand row is c + nc j with K index b.
+struct Scale {   // lambda(b, c, j) = s0 + sb D0[b] + sc D1[c] + sj D2[j]
+  const float *D0, *D1, *D2;
+  float s0, sb, sc, sj;
+};
+
+template <int FMT, int NT, int KIND>
+__device__ __forceinline__ void fd_epilogue(uint32_t tmem, typename tc::Op<FMT>::T *A, int na, int nb,
+                                            int nc, int Np, int ntile, const Scale &sc, double *so,
+                                            long long jstride) {
+  using namespace tc;
+  constexpr int G = NT / 128, T16 = Op<FMT>::T16;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
+  const int L = nb * nc, nch = (na + 7) >> 3, nit = ntile * nch;
+  const int lbo = (rup(nc * na, 128) + 1) * T16;   // K-chunk stride of the next operand
+  const int jstep = nc * T16;                       // next-operand offset per column j
+  for (int it = half; it < nit; it += G) {
+    const int t = it / nch, j0 = (it - t * nch) * 8;
+    uint32_t raw[8];
+    ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), raw);
+    ld_wait();
+    const int line = t * 128 + q * 32 + lane;
+    if (line >= L) continue;
+    const int jn = min(8, na - j0);
+    if (KIND == 2) {
+      double *o = so + line + jstride * j0;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (jj < jn) o[jstride * jj] = f32_to_f64(__uint_as_float(raw[jj]));
+    } else {
+      const int c = line / nb, b = line - c * nb;
+      // element (row = c + nc j, k = b) of the next operand
+      typename Op<FMT>::T *dst = A + kslab<FMT>(c + nc * j0, b, lbo);
+      float lb = 0.f;
+      if (KIND == 1) lb = sc.s0 + sc.sb * sc.D0[b] + sc.sc * sc.D1[c];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        if (jj < jn) {
+          float x = __uint_as_float(raw[jj]);
+          if (KIND == 1) x = __fdividef(x, lb + sc.sj * sc.D2[j0 + jj]);
+          dst[jj * jstep] = Op<FMT>::cvt(x);
+        }
+      }
+    }
+  }
+}
+
 template <int FMT, int NT>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, const Tab1D *tabs,
                                                const float *fpool, int dim, int interior,
@@ -69,7 +134,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
   // read it have completed by then), followed by the B operands
   T *A = reinterpret_cast<T *>(smraw);
   T *bm = A + cap;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   // the gate load overlaps the patch-descriptor loads
   const double gv = gate ? *gate : 1.0;
   const int k = plist[blockIdx.x], l = blockIdx.y;
@@ -91,6 +156,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
   if (tid == 0) {
     failed = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tma_bar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   __syncthreads();
@@ -120,38 +186,46 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
   {
     uint4 *z = reinterpret_cast<uint4 *>(A);
     const int nz = cap * (int)sizeof(T) / 16;
-    for (int i = tid; i < nz; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = tid; i < nz; i += NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   __syncthreads();
-  // load the tensor as the first operand: line = i2 + n2 i3, k = i1; the
-  // loads of a batch are all issued before the first shared-memory store
+  // load the tensor as the first operand (line = i2 + n2 i3, k = i1) in
+  // chunks of four K entries, chunk g = line * kq + kc; the (line, kc) of a
+  // thread's chunks step by NT without a division, and the loads of two
+  // steps are issued before their stores
   {
-    const int kch = rup(n[0], KSTEP) / T16;
-    const float inv = 1.0f / (float)n[0];
-    constexpr int LB = 16;
+    const int kq = (n[0] + 3) >> 2, nq = (N / n[0]) * kq;
+    const int lbo = (rup(N / n[0], 128) + 1) * T16;
+    const int dl = NT / kq, dk = NT - dl * kq;
+    int line = tid / kq, kc = tid - (tid / kq) * kq;
     const double *rb = r + base;
-    for (int i0 = tid; i0 < N; i0 += LB * NT) {
-      double v[LB];
+    for (int g0 = tid; g0 < nq; g0 += 2 * NT) {
+      double v[2][4];
+      int ln[2], kk[2];
 #pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int idx = i0 + u * NT;
-        v[u] = idx < N ? __ldg(rb + idx) : 0.0;
+      for (int u = 0; u < 2; ++u) {
+        ln[u] = line;
+        kk[u] = kc;
+        const bool in = g0 + u * NT < nq;
+        const double *p = rb + (long long)line * n[0] + 4 * kc;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[u][e] = (in && 4 * kc + e < n[0]) ? __ldg(p + e) : 0.0;
+        line += dl;
+        kc += dk;
+        if (kc >= kq) { kc -= kq; ++line; }
       }
 #pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int idx = i0 + u * NT;
-        if (idx < N) {
-          const int line = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
-          A[cmp<FMT>(line, idx - line * n[0], kch)] = Op<FMT>::cvt(f64_to_f32(v[u]));
+      for (int u = 0; u < 2; ++u) {
+        if (g0 + u * NT < nq) {
+          float f[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) f[e] = f64_to_op(v[u][e]);
+          st4<FMT>(&A[kslab<FMT>(ln[u], 4 * kk[u], lbo)], f);
         }
       }
     }
   }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  if (!wait_phase(&tma_bar, 0)) failed = 1;   // B operands have landed
+  if (tid == 0 && !wait_phase(&tma_bar, 0)) failed = 1;   // B operands have landed
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
                  "r"(tcols));
@@ -163,77 +237,49 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
 
-  // Lambda for this (patch, component)
-  const float hs = (float)pt.lscale, shf = (float)pt.lshift;
-  const float c0 = (float)P[k].lcf[l][0], c1 = (float)P[k].lcf[l][1], c2 = (float)P[k].lcf[l][2];
-  const float *Dv[3];
-  for (int d = 0; d < 3; ++d) {
-    const Tab1D tb = tabs[d == 0 ? lt0 : (d == 1 ? lt1 : lt2)];
-    Dv[d] = fpool + (interior ? tb.Di : tb.D);
-  }
-
   int na = n[0], nb = n[1], nc = n[2];   // current operand dims, a fastest
+#pragma unroll 1
   for (int m = 0; m < 6; ++m) {
-    const int L = nb * nc, ntile = rup(L, 128) / 128;
-    const int Kp = rup(na, KSTEP), Np = rup(na, 16), kch = Kp / T16;
+    const int ntile = rup(nb * nc, 128) / 128;
+    const int Kp = rup(na, KSTEP), Np = rup(na, 16);
+    // one thread issues the MMAs and waits for them; the others wait at the
+    // CTA barrier, which costs no issue slots
     if (tid == 0 && !failed) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t id = idesc(FMT, 128, Np);
-      const uint32_t sboA = (uint32_t)kch * kLBO, sboB = (uint32_t)kch * 128u;
+      const uint32_t lboA = (uint32_t)(ntile * 128 + 1) * 16u, sboB = (uint32_t)(Kp / T16) * 128u;
       const uint32_t a0 = smem_u32(A), b0 = smem_u32(bm + bslot(bs, m) * bsz);
       for (int t = 0; t < ntile; ++t)
         for (int ks = 0; ks < Kp / KSTEP; ++ks)
-          mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 16 * sboA + ks * 2 * kLBO, kLBO, sboA),
+          mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 2048u + ks * 2u * lboA, lboA, 128u),
                    sdesc(b0 + ks * 256, 128, sboB), id, ks > 0 ? 1u : 0u);
       commit(&mbar);
+      if (!wait_phase(&mbar, (uint32_t)(m & 1))) failed = 1;
+      asm volatile("tcgen05.fence::before_thread_sync;");
     }
-    if (!wait_phase(&mbar, (uint32_t)(m & 1))) failed = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
     if (failed) break;
-    // epilogue: D[line][j] -> next operand (rotated, in place) or the FP64
-    // output; work items are (tile, 8 columns), split between the NT / 128
-    // warps that share a TMEM lane quarter
-    constexpr int G = NT / 128;
-    const int q = warp & 3, half = warp >> 2;
-    const int nnb = nc, nkch = rup(nb, KSTEP) / T16;   // next operand: K = nb, lines = nc * na
-    const int nch = (na + 7) / 8, nit = ntile * nch;
-    // items it = half, half + G, ...: two TMEM loads in flight per wait
-    for (int it0 = half; it0 < nit; it0 += 2 * G) {
-      uint32_t raw[2][8];
-#pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        const int it = it0 + G * w;
-        if (it < nit) {
-          const int t = it / nch, j0 = (it - t * nch) * 8;
-          ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), raw[w]);
-        }
+    if (m == 5)
+      fd_epilogue<FMT, NT, 2>(tmem, A, na, nb, nc, Np, ntile, Scale{}, s + base,
+                              (long long)n[0] * n[1]);
+    else if (m == 2) {
+      // Lambda for this (patch, component), element (a1 = b, a2 = c,
+      // a3 = j): hs (c0 D0[b] + c1 D1[c] + c2 D2[j] + shift) for the full
+      // pencil, without hs and shift for the interior one; 2D problems have
+      // no third term (their third table is the one-function dummy)
+      const float hs = interior ? 1.f : (float)pt.lscale, shf = interior ? 0.f : (float)pt.lshift;
+      const float c0 = (float)P[k].lcf[l][0], c1 = (float)P[k].lcf[l][1];
+      const float c2 = dim == 3 ? (float)P[k].lcf[l][2] : 0.f;
+      const float *Dv[3];
+      for (int d = 0; d < 3; ++d) {
+        const Tab1D &tb = tabs[d == 0 ? lt0 : (d == 1 ? lt1 : lt2)];
+        Dv[d] = fpool + (interior ? tb.Di : tb.D);
       }
-      ld_wait();
-#pragma unroll
-      for (int w = 0; w < 2; ++w) {
-        const int it = it0 + G * w;
-        if (it >= nit) break;
-        const int t = it / nch, j0 = (it - t * nch) * 8;
-        const int line = t * 128 + q * 32 + lane;
-        if (line >= L) continue;
-        const int c = line / nb, b = line - c * nb;
-        float lb = 0.f;
-        if (m == 2) lb = c0 * Dv[0][b] + (dim == 3 ? c1 * Dv[1][c] : 0.f);
-#pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int j = j0 + jj;
-          if (j >= na) break;
-          float x = __uint_as_float(raw[w][jj]);
-          if (m == 2) {   // element r~(a1 = b, a2 = c, a3 = j): scale by Lambda^{-1}
-            float lam = (dim == 3) ? lb + c2 * Dv[2][j] : c0 * Dv[0][b] + c1 * Dv[1][c];
-            if (!interior) lam = hs * (lam + shf);
-            x = __fdividef(x, lam);
-          }
-          if (m == 5) s[base + line + (long long)n[0] * n[1] * j] = f32_to_f64(x);
-          else A[cmp<FMT>(c + nnb * j, b, nkch)] = Op<FMT>::cvt(x);
-        }
-      }
+      const Scale sc{Dv[0], Dv[1], Dv[2], hs * shf, hs * c0, hs * c1, hs * c2};
+      fd_epilogue<FMT, NT, 1>(tmem, A, na, nb, nc, Np, ntile, sc, nullptr, 0);
+    } else {
+      fd_epilogue<FMT, NT, 0>(tmem, A, na, nb, nc, Np, ntile, Scale{}, nullptr, 0);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -243,9 +289,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
     na = nb; nb = nc; nc = t0;
   }
   if (failed) {   // give MMAs still in flight one more bounded wait before freeing TMEM
-    for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0)
+      for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
   }
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
@@ -259,7 +307,7 @@ static int g_tc_dyn_max, g_slab_dyn_max;
 struct TcNeed { int cap, bsz, tcols, nslot; bool ok; };
 
 static TcNeed tc_need(const DevPatch &p, int interior, int fmt) {
-  const int kstep = (fmt == 2) ? 8 : 16, t16 = (fmt == 2) ? 4 : 8;
+  const int kstep = (fmt == 2) ? 8 : 16;
   TcNeed t{0, 0, 32, 1, true};
   for (int l = 0; l < 3; ++l)
     t.nslot = std::max(t.nslot, (int)(b_slots(p.ltab[l][0], p.ltab[l][1], p.ltab[l][2]) >> 24));
@@ -268,14 +316,14 @@ static TcNeed tc_need(const DevPatch &p, int interior, int fmt) {
   for (int d = 0; d < 3; ++d) {
     const int na = n[d], nb = n[(d + 1) % 3], nc = n[(d + 2) % 3];
     const int Lp = tc::rup(nb * nc, 128), Kp = tc::rup(na, kstep), Np = tc::rup(na, 16);
-    t.cap = std::max(t.cap, (Lp / 8) * (Kp / t16) * 9 * t16);   // padded core matrices
+    t.cap = std::max(t.cap, Kp * (Lp + 1));   // K-chunk slabs of Lp + 1 rows
+    if (Lp + 1 >= (1 << 14)) t.ok = false;    // chunk stride within the descriptor field
     t.bsz = std::max(t.bsz, Np * Kp);
     const int cols = (Lp / 128) * Np;
     while (t.tcols < cols) t.tcols *= 2;
     if (Np > 256) t.ok = false;
   }
   if (t.tcols > 512) t.ok = false;
-  if (n[0] * n[1] * n[2] >= (1 << 20)) t.ok = false;   // exact float index split
   return t;
 }
 

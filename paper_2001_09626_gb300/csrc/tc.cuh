@@ -105,6 +105,40 @@ template <> struct Op<1> {   // BF16: 8 elements per 16 bytes, 16 per MMA
 
 __host__ __device__ __forceinline__ int rup(int x, int m) { return (x + m - 1) / m * m; }
 
+// FP64 -> FP32 for a value that only becomes a tensor-core operand, on the
+// integer pipes: the FP32 significand is truncated rather than rounded, which
+// the operand rounding to TF32 (10 stored bits) or BF16 (7) makes immaterial.
+// Magnitudes below the FP32 normal range flush to signed zero, finite ones
+// above it become +-inf, NaN stays NaN.
+__device__ __forceinline__ float f64_to_op(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned mag = hi & 0x7FFFFFFFu;
+  unsigned r = ((mag - (896u << 20)) << 3) | (lo >> 29);
+  r = mag < (897u << 20) ? 0u : r;
+  r = mag >= (1151u << 20) ? 0x7F800000u : r;
+  r = (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull ? 0x7FC00000u : r;
+  return __uint_as_float(r | (hi & 0x80000000u));
+}
+
+// four (two) consecutive K entries of one operand row, 16-byte (8-byte)
+// aligned for TF32, 8-byte (4-byte) for BF16
+template <int FMT> __device__ __forceinline__ void st4(typename Op<FMT>::T *p, const float *v);
+template <> __device__ __forceinline__ void st4<2>(float *p, const float *v) {
+  *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <> __device__ __forceinline__ void st4<1>(__nv_bfloat16 *p, const float *v) {
+  __nv_bfloat162 h[2] = {__floats2bfloat162_rn(v[0], v[1]), __floats2bfloat162_rn(v[2], v[3])};
+  *reinterpret_cast<uint2 *>(p) = *reinterpret_cast<const uint2 *>(h);
+}
+template <int FMT> __device__ __forceinline__ void st2(typename Op<FMT>::T *p, const float *v);
+template <> __device__ __forceinline__ void st2<2>(float *p, const float *v) {
+  *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+template <> __device__ __forceinline__ void st2<1>(__nv_bfloat16 *p, const float *v) {
+  *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v[0], v[1]);
+}
+
 // element offset of (row, k) in the canonical K-major core-matrix layout with
 // Kp columns (core matrices 128 bytes apart); used for the prebuilt B operands
 template <int FMT>
