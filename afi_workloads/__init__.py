@@ -208,17 +208,25 @@ def config(name: str, seed: int = 0) -> Problem:
         {12,16,24,32,48}, one degree drawn from {2,3,4,5} (conforming draws).
     C4  quarter annulus 6x4x3 patches, p=3, 24^3 elements.
     C5  twisted box 8x8x4 patches, p=4, 48^3 elements.
-    Small variants (``*-small``) keep the geometry kind at oracle-friendly sizes.
+    Small variants (``*-small``, ``*-mid``) keep the geometry kind at oracle-friendly
+    sizes; ``C2-quarter`` and ``C3-quarter`` hold a few full-size patches of C2 / C3.
     """
     if name == "C1":
         return unit_box(2, (2, 2), 2, 8, name="C1")
     if name == "C2":
         return unit_box(3, (4, 4, 4), 3, 16, jitter=0.1, seed=seed, name="C2")
-    if name == "C3":
+    if name in ("C3", "C3-quarter"):
         rng = np.random.default_rng(np.random.SeedSequence(seed).spawn(3)[1])
         grid = (6, 4, 3)
         cols = [[int(rng.choice(NEL_CHOICES)) for _ in range(grid[l])] for l in range(3)]
         p = int(rng.choice(P_CHOICES))
+        if name == "C3-quarter":
+            # nine of C3's patches, one per distinct (direction 1, direction 2)
+            # column width, in one column of direction 3
+            firsts = [sorted({c: i for i, c in reversed(list(enumerate(cols[l])))}.values())
+                      for l in range(2)]
+            sub = [[cols[0][i] for i in firsts[0]], [cols[1][i] for i in firsts[1]], cols[2][:1]]
+            return quarter_annulus(tuple(len(c) for c in sub), p, nel_cols=sub, name=name)
         return quarter_annulus(grid, p, nel_cols=cols, name="C3")
     if name == "C4":
         return quarter_annulus((6, 4, 3), 3, 24, name="C4")
@@ -231,6 +239,8 @@ def config(name: str, seed: int = 0) -> Problem:
         return unit_box(3, (2, 2, 3), 3, 16, jitter=0.1, seed=seed, name=name)
     if name == "C2-mid":
         return unit_box(3, (3, 3, 3), 3, 6, jitter=0.1, seed=seed, name=name)
+    if name == "C3-mid":   # uneven columns at C3's degree, oracle-sized
+        return quarter_annulus((2, 2, 1), 4, nel_cols=[[4, 6], [4, 6], [4]], name=name)
     if name == "C4-small":
         return quarter_annulus((3, 2, 2), 3, 3, name=name)
     if name == "C5-small":

@@ -81,36 +81,51 @@ __device__ __forceinline__ void fd_epilogue(uint32_t tmem, typename tc::Op<FMT>:
   using namespace tc;
   constexpr int G = NT / 128, T16 = Op<FMT>::T16;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3, half = warp >> 2;
-  const int L = nb * nc, nch = (na + 7) >> 3, nit = ntile * nch;
+  const int L = nb * nc, nch = (na + 7) >> 3;
   const int lbo = (rup(nc * na, 128) + 1) * T16;   // K-chunk stride of the next operand
   const int jstep = nc * T16;                       // next-operand offset per column j
-  for (int it = half; it < nit; it += G) {
-    const int t = it / nch, j0 = (it - t * nch) * 8;
+  // the warp's items (t, ch) = (it / nch, it % nch), it = half, half + G,
+  // ..., and its lane's line = b + nb c, stepped without divisions
+  int t = 0, ch = half;
+  while (ch >= nch) { ch -= nch; ++t; }
+  int line = t * 128 + q * 32 + lane;
+  int c = line / nb, b = line - c * nb;
+  const int dq = 128 / nb, dr = 128 - dq * nb;
+  while (t < ntile) {
+    const int j0 = ch * 8;
     uint32_t raw[8];
     ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), raw);
     ld_wait();
-    const int line = t * 128 + q * 32 + lane;
-    if (line >= L) continue;
-    const int jn = min(8, na - j0);
-    if (KIND == 2) {
-      double *o = so + line + jstride * j0;
+    if (line < L) {
+      const int jn = min(8, na - j0);
+      if (KIND == 2) {
+        double *o = so + line + jstride * j0;
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj)
-        if (jj < jn) o[jstride * jj] = f32_to_f64(__uint_as_float(raw[jj]));
-    } else {
-      const int c = line / nb, b = line - c * nb;
-      // element (row = c + nc j, k = b) of the next operand
-      typename Op<FMT>::T *dst = A + kslab<FMT>(c + nc * j0, b, lbo);
-      float lb = 0.f;
-      if (KIND == 1) lb = sc.s0 + sc.sb * sc.D0[b] + sc.sc * sc.D1[c];
+        for (int jj = 0; jj < 8; ++jj)
+          if (jj < jn) o[jstride * jj] = f32_to_f64(__uint_as_float(raw[jj]));
+      } else {
+        // element (row = c + nc j, k = b) of the next operand
+        typename Op<FMT>::T *dst = A + kslab<FMT>(c + nc * j0, b, lbo);
+        float lb = 0.f;
+        if (KIND == 1) lb = sc.s0 + sc.sb * sc.D0[b] + sc.sc * sc.D1[c];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) {
-        if (jj < jn) {
-          float x = __uint_as_float(raw[jj]);
-          if (KIND == 1) x = __fdividef(x, lb + sc.sj * sc.D2[j0 + jj]);
-          dst[jj * jstep] = Op<FMT>::cvt(x);
+        for (int jj = 0; jj < 8; ++jj) {
+          if (jj < jn) {
+            float x = __uint_as_float(raw[jj]);
+            if (KIND == 1) x = __fdividef(x, lb + sc.sj * sc.D2[j0 + jj]);
+            dst[jj * jstep] = Op<FMT>::cvt(x);
+          }
         }
       }
+    }
+    ch += G;
+    while (ch >= nch) {   // next tile: line += 128
+      ch -= nch;
+      ++t;
+      line += 128;
+      c += dq;
+      b += dr;
+      if (b >= nb) { b -= nb; ++c; }
     }
   }
 }

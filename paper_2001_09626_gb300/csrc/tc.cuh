@@ -106,19 +106,19 @@ template <> struct Op<1> {   // BF16: 8 elements per 16 bytes, 16 per MMA
 __host__ __device__ __forceinline__ int rup(int x, int m) { return (x + m - 1) / m * m; }
 
 // FP64 -> FP32 for a value that only becomes a tensor-core operand, on the
-// integer pipes: the FP32 significand is truncated rather than rounded, which
-// the operand rounding to TF32 (10 stored bits) or BF16 (7) makes immaterial.
-// Magnitudes below the FP32 normal range flush to signed zero, finite ones
-// above it become +-inf, NaN stays NaN.
+// integer pipes and from the high word alone: the FP32 significand keeps the
+// top 20 bits of the FP64 one (truncated), which the operand rounding to
+// TF32 (10 stored bits) or BF16 (7) makes immaterial.  The exponent is
+// clamped: magnitudes below 2^-127 give signed zero, those in [2^-127,
+// 2^-126) an FP32 subnormal below 2^-126, those of 2^128 and above +-inf;
+// NaN stays NaN.
 __device__ __forceinline__ float f64_to_op(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned hi = (unsigned)__double2hiint(x);
   const unsigned mag = hi & 0x7FFFFFFFu;
-  unsigned r = ((mag - (896u << 20)) << 3) | (lo >> 29);
-  r = mag < (897u << 20) ? 0u : r;
-  r = mag >= (1151u << 20) ? 0x7F800000u : r;
-  r = (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull ? 0x7FC00000u : r;
-  return __uint_as_float(r | (hi & 0x80000000u));
+  const unsigned m = min(max(mag, 0x38000000u), 0x47F00000u);
+  unsigned r = ((m - 0x38000000u) << 3) | (hi & 0x80000000u);
+  if (mag > 0x7FF00000u) r |= 0x00400000u;
+  return __uint_as_float(r);
 }
 
 // four (two) consecutive K entries of one operand row, 16-byte (8-byte)
