@@ -150,6 +150,8 @@ struct TcSplit {
   // three-pass tensor-core FD for tensors larger than one CTA (fd_slab.cu)
   void *d_plane = nullptr, *d_line = nullptr;   // int4 / int2 work lists
   int nplane = 0, nline = 0;
+  int *d_pbounds = nullptr, *d_lbounds = nullptr;   // persistent CTAs' ranges of the lists
+  int pgrid = 0, lgrid = 0;                         // persistent CTAs per (component, rhs)
   int cap_p = 0, bsz_p = 0, tcols_p = 32, cap_l = 0, bsz_l = 0, tcols_l = 32;
   size_t smem_p = 0, smem_l = 0;
 };

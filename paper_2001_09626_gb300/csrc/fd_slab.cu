@@ -16,7 +16,12 @@
 // is 8 + 4 + 4 + 4 + 4 + 8 = 32 bytes per DoF (TF32/BF16 operands, FP32
 // scratch) against the 16 of a single-pass kernel.  Each MMA is a GEMM
 // D[line][j] = sum_k A[line][k] B[j][k] with the tensor as the K-major A
-// operand (lines on the 128 TMEM lanes) and U^T or U as B, staged by TMA.
+// operand (lines on the 128 TMEM lanes, one slab per 16-byte K chunk with
+// rows 16 bytes apart) and U^T or U as B, staged by TMA.  Each CTA works
+// through a short range of the pass's work list (about two items, ranges of
+// equal cost), allocating tensor memory, initialising its barriers and
+// loading the B operands once per range; one thread issues and waits for
+// the MMAs while the others wait at the CTA barrier.
 #include "tc.cuh"
 
 #include <algorithm>
@@ -28,26 +33,26 @@ using namespace tc;
 
 namespace {
 
-// Issue the MMAs of one product: ntile tiles of 128 lines of the padded
-// tensor operand A (K-major, kLBO-padded), against the canonical B operand
-// (Np x Kp) at b, accumulating into TMEM columns t * Np.
+// Issue the MMAs of one product: ntile tiles of 128 lines of the tensor
+// operand A (K-major, one slab per 16-byte K chunk: rows 16 bytes apart,
+// chunks lbo bytes apart), against the canonical B operand (Np x Kp) at b,
+// accumulating into TMEM columns t * Np.
 template <int FMT>
 __device__ __forceinline__ void issue_product(uint32_t tmem, const void *A, const void *B, int ntile,
-                                              int Kp, int Np) {
+                                              int Kp, int Np, uint32_t lbo) {
   constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t id = idesc(FMT, 128, Np);
-  const int kch = Kp / T16;
-  const uint32_t sboA = (uint32_t)kch * kLBO, sboB = (uint32_t)kch * 128u;
+  const uint32_t sboB = (uint32_t)(Kp / T16) * 128u;
   const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
   for (int t = 0; t < ntile; ++t)
     for (int ks = 0; ks < Kp / KSTEP; ++ks)
-      mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 16 * sboA + ks * 2 * kLBO, kLBO, sboA),
+      mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 2048u + ks * 2u * lbo, lbo, 128u),
                sdesc(b0 + ks * 256, 128, sboB), id, ks > 0 ? 1u : 0u);
 }
 
 // Stage the B operands of two products (prebuilt canonical layout in
-// tcpool) into slots bm and bm + bsz, and start the operand-buffer fill.
+// tcpool) into slots bm and bm + bsz.
 template <typename T>
 __device__ __forceinline__ void stage_b(uint64_t *bar, T *bm, int bsz, const unsigned char *tcpool,
                                         long long off0, uint32_t bytes0, long long off1,
@@ -84,15 +89,18 @@ __device__ __forceinline__ void st_out(float *p, float v) { *p = v; }
 }  // namespace
 
 // Passes A (BACK = 0: U_1^T then U_2^T, FP64 in, FP32 out) and C (BACK = 1:
-// U_1 then U_2, FP32 in, FP64 out) on nz planes of one (patch, component,
-// right-hand side) tensor.  work[blockIdx.x] = (patch, first plane, nz).
+// U_1 then U_2, FP32 in, FP64 out).  Work items (patch, first plane, nz
+// planes) of one component (blockIdx.y) and right-hand side (blockIdx.z); a
+// CTA takes the items [bounds[x], bounds[x + 1]) (ranges of equal cost) and
+// keeps its tensor memory, barriers and, while the tables stay the same, its
+// B operands from one item to the next.
 template <int FMT, int BACK>
-__global__ void __launch_bounds__(256, 4) k_fd_plane(const DevPatch *P, const Tab1D *tabs,
-                                                     const int4 *work, int interior,
-                                                     const double *r, float *scr, double *s,
-                                                     long long rhs_stride, int cap, int bsz,
-                                                     int tcols, const double *gate, int *err,
-                                                     const unsigned char *tcpool) {
+__global__ void __launch_bounds__(256, 3) k_fd_plane(const DevPatch *P, const Tab1D *tabs,
+                                                     const int4 *work, const int *bounds,
+                                                     int interior, const double *r, float *scr,
+                                                     double *s, long long rhs_stride, int cap,
+                                                     int bsz, int tcols, const double *gate,
+                                                     int *err, const unsigned char *tcpool) {
   using T = typename Op<FMT>::T;
   using TIn = typename std::conditional<BACK == 0, double, float>::type;
   constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
@@ -105,17 +113,9 @@ __global__ void __launch_bounds__(256, 4) k_fd_plane(const DevPatch *P, const Ta
   T *bm = A + cap;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double gv = gate ? *gate : 1.0;
-  const int4 w = work[blockIdx.x];
+  const int w0 = bounds[blockIdx.x], w1 = bounds[blockIdx.x + 1];
   const int l = blockIdx.y;
-  const DevPatch pt = P[w.x];
-  if (gv == 0.0) return;   // inactive MINRES iteration
-  const int n1 = interior ? pt.ni[0] : pt.n[0], n2 = interior ? pt.ni[1] : pt.n[1];
-  const int n3 = interior ? pt.ni[2] : pt.n[2];
-  const int z0 = w.y, nz = w.z;
-  const long long plane = (long long)n1 * n2;
-  const long long base = (interior ? pt.ioff : pt.off) + (long long)l * plane * n3 +
-                         (long long)blockIdx.z * rhs_stride + z0 * plane;
-  const TIn *in = BACK ? (const TIn *)(const void *)(scr + base) : (const TIn *)(const void *)(r + base);
+  if (gv == 0.0 || w0 >= w1) return;   // inactive MINRES iteration / empty range
 
   if (tid == 0) {
     failed = 0;
@@ -124,166 +124,199 @@ __global__ void __launch_bounds__(256, 4) k_fd_plane(const DevPatch *P, const Ta
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   __syncthreads();
-  // both products use one B slot when directions 1 and 2 share a table
-  // this component's tables, read from global memory (not from the local
-  // copy, which a runtime index would move to local memory)
-  const int lt0 = P[w.x].ltab[l][0], lt1 = P[w.x].ltab[l][1];
-  const int slot1 = (lt0 == lt1) ? 0 : 1;
-  if (tid == 0) {
-    const uint32_t b0 = (uint32_t)(rup(n1, 16) * rup(n1, KSTEP) * (int)sizeof(T));
-    const uint32_t b1 = (uint32_t)(rup(n2, 16) * rup(n2, KSTEP) * (int)sizeof(T));
-    expect_tx(&tma_bar, slot1 ? b0 + b1 : b0);
-    bulk_g2s(bm, tcpool + tabs[lt0].tcB[FMT == 1][interior][BACK], b0, &tma_bar);
-    if (slot1) bulk_g2s(bm + bsz, tcpool + tabs[lt1].tcB[FMT == 1][interior][BACK], b1, &tma_bar);
-  }
-  {
-    uint4 *zp = reinterpret_cast<uint4 *>(A);
-    const int nzero = cap * (int)sizeof(T) / 16;
-    for (int i = tid; i < nzero; i += 256) zp[i] = make_uint4(0u, 0u, 0u, 0u);
-  }
-  __syncthreads();
-  // first operand: row = i2 + n2 * zl, k = i1 (the slice is contiguous)
-  const int kch0 = rup(n1, KSTEP) / T16, N = (int)(plane * nz);
-  const float inv = 1.0f / (float)n1;
-  if ((n1 & 3) == 0 && ((uintptr_t)in & 15) == 0) {
-    // four consecutive i1 of one row per thread: 16-byte global loads and
-    // one 16-byte (TF32) or 8-byte (BF16) shared store
-    constexpr int LB = 8;
-    const int N4 = N >> 2;
-    for (int g0 = tid; g0 < N4; g0 += LB * 256) {
-      float v[LB][4];
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int g = g0 + u * 256;
-        if (g < N4) ld4(in + 4 * g, v[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int g = g0 + u * 256;
-        if (g < N4) {
-          const int idx = 4 * g;
-          const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
-          st4<FMT>(&A[cmp<FMT>(row, idx - row * n1, kch0)], v[u]);
-        }
-      }
-    }
-  } else if ((n1 & 1) == 0 && ((uintptr_t)in & (2 * sizeof(TIn) - 1)) == 0) {
-    // two consecutive i1 of one row per thread (even rows): 2-element
-    // global loads and one 8-byte (TF32) or 4-byte (BF16) shared store
-    constexpr int LB = 8;
-    const int N2 = N >> 1;
-    for (int g0 = tid; g0 < N2; g0 += LB * 256) {
-      float v[LB][2];
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int g = g0 + u * 256;
-        if (g < N2) ld2(in + 2 * g, v[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int g = g0 + u * 256;
-        if (g < N2) {
-          const int idx = 2 * g;
-          const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
-          st2<FMT>(&A[cmp<FMT>(row, idx - row * n1, kch0)], v[u]);
-        }
-      }
-    }
-  } else {
-    const int kch = kch0;
-    constexpr int LB = 16;
-    for (int i0 = tid; i0 < N; i0 += LB * 256) {
-      float v[LB];
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int idx = i0 + u * 256;
-        v[u] = idx < N ? ld_in(in + idx) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int idx = i0 + u * 256;
-        if (idx < N) {
-          const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
-          A[cmp<FMT>(row, idx - row * n1, kch)] = Op<FMT>::cvt(v[u]);
-        }
-      }
-    }
-  }
-  if (!wait_phase(&tma_bar, 0)) failed = 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
                  "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
   const int q = warp & 3, half = warp >> 2;
+  int key = -1;            // tables of the B operands held in shared memory
+  uint32_t tma_phase = 0;
 
-  for (int m = 0; m < 2; ++m) {
-    const int na = m ? n2 : n1, nb = m ? n1 : n2;   // contracted size, other in-plane size
-    const int L = nb * nz, ntile = rup(L, 128) / 128;
-    const int Kp = rup(na, KSTEP), Np = rup(na, 16);
-    if (tid == 0 && !failed) {
-      issue_product<FMT>(tmem, A, bm + (m ? slot1 : 0) * bsz, ntile, Kp, Np);
-      commit(&mbar);
+  for (int wi = w0; wi < w1; ++wi) {
+    const int4 w = work[wi];
+    const DevPatch &pg = P[w.x];
+    const int n1 = interior ? pg.ni[0] : pg.n[0], n2 = interior ? pg.ni[1] : pg.n[1];
+    const int n3 = interior ? pg.ni[2] : pg.n[2];
+    const int z0 = w.y, nz = w.z;
+    const long long plane = (long long)n1 * n2;
+    const long long base = (interior ? pg.ioff : pg.off) + (long long)l * plane * n3 +
+                           (long long)blockIdx.z * rhs_stride + z0 * plane;
+    const TIn *in = BACK ? (const TIn *)(const void *)(scr + base) : (const TIn *)(const void *)(r + base);
+    // this component's tables, read from global memory (a runtime index
+    // into a local copy would move it to local memory)
+    const int lt0 = pg.ltab[l][0], lt1 = pg.ltab[l][1];
+    const int slot1 = (lt0 == lt1) ? 0 : 1;
+    const int nkey = lt0 * 65536 + lt1;
+    const bool reload = nkey != key;
+    if (reload && tid == 0) {   // both products use one slot when the tables agree
+      const uint32_t b0 = (uint32_t)(rup(n1, 16) * rup(n1, KSTEP) * (int)sizeof(T));
+      const uint32_t b1 = (uint32_t)(rup(n2, 16) * rup(n2, KSTEP) * (int)sizeof(T));
+      expect_tx(&tma_bar, slot1 ? b0 + b1 : b0);
+      bulk_g2s(bm, tcpool + tabs[lt0].tcB[FMT == 1][interior][BACK], b0, &tma_bar);
+      if (slot1) bulk_g2s(bm + bsz, tcpool + tabs[lt1].tcB[FMT == 1][interior][BACK], b1, &tma_bar);
     }
-    if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    // a fresh zero operand per item: no value of the previous item (a NaN
+    // included) may reach this item's K padding
+    {
+      uint4 *zp = reinterpret_cast<uint4 *>(A);
+      const int nzero = cap * (int)sizeof(T) / 16;
+      for (int i = tid; i < nzero; i += 256) zp[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     __syncthreads();
-    if (failed) break;
-    // m = 0: D[row = i2 + n2 zl][j = a1] -> A[row' = a1 + n1 zl][k = i2]
-    // m = 1: D[row = a1 + n1 zl][j = a2] -> out[zl][a2][a1]
-    const int nkch = rup(n2, KSTEP) / T16;
-    const int nch = (na + 7) / 8, nit = ntile * nch;
-    for (int it0 = half; it0 < nit; it0 += 4) {
-      uint32_t raw[2][8];
+    // first operand: row = i2 + n2 * zl, k = i1 (the slice is contiguous)
+    const int lbo0 = (rup(n2 * nz, 128) + 1) * T16, N = (int)(plane * nz);
+    const float inv = 1.0f / (float)n1;
+    if ((n1 & 3) == 0 && ((uintptr_t)in & 15) == 0) {
+      // four consecutive i1 of one row per thread: 16-byte global loads and
+      // one 16-byte (TF32) or 8-byte (BF16) shared store
+      constexpr int LB = 4;
+      const int N4 = N >> 2;
+      for (int g0 = tid; g0 < N4; g0 += LB * 256) {
+        float v[LB][4];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int it = it0 + 2 * u;
-        if (it < nit) {
-          const int t = it / nch, j0 = (it - t * nch) * 8;
-          ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), raw[u]);
+        for (int u = 0; u < LB; ++u) {
+          const int g = g0 + u * 256;
+          if (g < N4) ld4(in + 4 * g, v[u]);
         }
-      }
-      ld_wait();
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int it = it0 + 2 * u;
-        if (it >= nit) break;
-        const int t = it / nch, j0 = (it - t * nch) * 8;
-        const int row = t * 128 + q * 32 + lane;
-        if (row >= L) continue;
-        const int zl = row / nb, b = row - zl * nb;
-        if (m == 0) {
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int j = j0 + jj;
-            if (j >= na) break;
-            A[cmp<FMT>(j + n1 * zl, b, nkch)] = Op<FMT>::cvt(__uint_as_float(raw[u][jj]));
-          }
-        } else {
-          const long long ob = base + (long long)zl * plane + b;
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int j = j0 + jj;
-            if (j >= na) break;
-            if (BACK) st_out(s + ob + (long long)j * n1, __uint_as_float(raw[u][jj]));
-            else st_out(scr + ob + (long long)j * n1, __uint_as_float(raw[u][jj]));
+        for (int u = 0; u < LB; ++u) {
+          const int g = g0 + u * 256;
+          if (g < N4) {
+            const int idx = 4 * g;
+            const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
+            st4<FMT>(&A[kslab<FMT>(row, idx - row * n1, lbo0)], v[u]);
           }
         }
       }
+    } else if ((n1 & 1) == 0 && ((uintptr_t)in & (2 * sizeof(TIn) - 1)) == 0) {
+      // two consecutive i1 of one row per thread (even rows): 2-element
+      // global loads and one 8-byte (TF32) or 4-byte (BF16) shared store
+      constexpr int LB = 4;
+      const int N2 = N >> 1;
+      for (int g0 = tid; g0 < N2; g0 += LB * 256) {
+        float v[LB][2];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int g = g0 + u * 256;
+          if (g < N2) ld2(in + 2 * g, v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int g = g0 + u * 256;
+          if (g < N2) {
+            const int idx = 2 * g;
+            const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
+            st2<FMT>(&A[kslab<FMT>(row, idx - row * n1, lbo0)], v[u]);
+          }
+        }
+      }
+    } else {
+      constexpr int LB = 8;
+      for (int i0 = tid; i0 < N; i0 += LB * 256) {
+        float v[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int idx = i0 + u * 256;
+          v[u] = idx < N ? ld_in(in + idx) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int idx = i0 + u * 256;
+          if (idx < N) {
+            const int row = __float2int_rz(__fmul_rn(__fadd_rn((float)idx, 0.5f), inv));
+            A[kslab<FMT>(row, idx - row * n1, lbo0)] = Op<FMT>::cvt(v[u]);
+          }
+        }
+      }
+    }
+    if (reload) {   // the B operands have landed
+      if (tid == 0 && !wait_phase(&tma_bar, tma_phase)) failed = 1;
+      tma_phase ^= 1u;
+      key = nkey;
     }
     asm volatile("fence.proxy.async.shared::cta;");
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (failed) break;
+
+    for (int m = 0; m < 2; ++m) {
+      const int na = m ? n2 : n1, nb = m ? n1 : n2;   // contracted size, other in-plane size
+      const int L = nb * nz, ntile = rup(L, 128) / 128;
+      const int Kp = rup(na, KSTEP), Np = rup(na, 16);
+      // one thread issues the MMAs and waits for them (two commits per item:
+      // phase parity m); the others wait at the CTA barrier
+      if (tid == 0 && !failed) {
+        issue_product<FMT>(tmem, A, bm + (m ? slot1 : 0) * bsz, ntile, Kp, Np,
+                           (uint32_t)(ntile * 128 + 1) * 16u);
+        commit(&mbar);
+        if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+      }
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (failed) break;
+      // m = 0: D[line = i2 + n2 zl][j = a1] -> A[row = a1 + n1 zl][k = i2]
+      // m = 1: D[line = a1 + n1 zl][j = a2] -> out[zl][a2][a1]
+      // items (t, ch) = (it / nch, it % nch), it = half, half + 2, ...; the
+      // lane's line = b + nb zl is stepped without divisions
+      const int lbo1 = (rup(n1 * nz, 128) + 1) * T16;
+      const int nch = (na + 7) >> 3;
+      int t = 0, ch = half;
+      while (ch >= nch) { ch -= nch; ++t; }
+      int line = t * 128 + q * 32 + lane;
+      int zl = line / nb, b = line - zl * nb;
+      const int dq = 128 / nb, dr = 128 - dq * nb;
+      while (t < ntile) {
+        const int j0 = ch * 8;
+        uint32_t raw[8];
+        ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(t * Np + j0), raw);
+        ld_wait();
+        if (line < L) {
+          const int jn = min(8, na - j0);
+          if (m == 0) {
+            T *dst = A + kslab<FMT>(j0 + n1 * zl, b, lbo1);
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+              if (jj < jn) dst[jj * T16] = Op<FMT>::cvt(__uint_as_float(raw[jj]));
+          } else {
+            const long long ob = base + (long long)zl * plane + b + (long long)j0 * n1;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              if (jj < jn) {
+                if (BACK) st_out(s + ob + (long long)jj * n1, __uint_as_float(raw[jj]));
+                else st_out(scr + ob + (long long)jj * n1, __uint_as_float(raw[jj]));
+              }
+            }
+          }
+        }
+        ch += 2;
+        while (ch >= nch) {   // next tile: line += 128
+          ch -= nch;
+          ++t;
+          line += 128;
+          zl += dq;
+          b += dr;
+          if (b >= nb) { b -= nb; ++zl; }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
+    }
+    if (failed) break;
   }
   if (failed) {   // one more bounded wait for MMAs in flight before freeing TMEM
-    for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0)
+      for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
   }
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
@@ -291,17 +324,21 @@ __global__ void __launch_bounds__(256, 4) k_fd_plane(const DevPatch *P, const Ta
 }
 
 // Pass B: for 128 consecutive lines (a1 + n1 a2) of one tensor in the FP32
-// scratch, t = U_3^T x along i3, t /= Lambda, x = U_3 t, in place.
-// work[blockIdx.x] = (patch, first line).
+// scratch, t = U_3^T x along i3, t /= Lambda, x = U_3 t, in place.  Work
+// items (patch, first line) of one component (blockIdx.y) and right-hand
+// side (blockIdx.z); a CTA takes the items [bounds[x], bounds[x + 1]) and
+// keeps its tensor memory, barriers and, while the table stays the same, its
+// B operands.
 template <int FMT>
-__global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab1D *tabs,
+__global__ void __launch_bounds__(256, 3) k_fd_line(const DevPatch *P, const Tab1D *tabs,
                                                     const float *fpool, const int2 *work,
-                                                    int interior, float *scr,
+                                                    const int *bounds, int interior, float *scr,
                                                     long long rhs_stride, int cap, int bsz,
                                                     int tcols, const double *gate, int *err,
                                                     const unsigned char *tcpool) {
   using T = typename Op<FMT>::T;
   constexpr int KSTEP = Op<FMT>::KSTEP, T16 = Op<FMT>::T16;
+  constexpr int lbo = 129 * T16;   // one 128-line tile: K chunks (128 + 1) x 16 bytes apart
   extern __shared__ __align__(1024) unsigned char smraw[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ __align__(8) uint64_t tma_bar;
@@ -311,15 +348,9 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
   T *bm = A + cap;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double gv = gate ? *gate : 1.0;
-  const int2 w = work[blockIdx.x];
+  const int w0 = bounds[blockIdx.x], w1 = bounds[blockIdx.x + 1];
   const int l = blockIdx.y;
-  const DevPatch pt = P[w.x];
-  if (gv == 0.0) return;   // inactive MINRES iteration
-  const int n1 = interior ? pt.ni[0] : pt.n[0], n2 = interior ? pt.ni[1] : pt.n[1];
-  const int n3 = interior ? pt.ni[2] : pt.n[2];
-  const int LN = n1 * n2, line0 = w.y, nl = min(128, LN - line0);
-  float *X = scr + (interior ? pt.ioff : pt.off) + (long long)l * LN * n3 +
-             (long long)blockIdx.z * rhs_stride + line0;
+  if (gv == 0.0 || w0 >= w1) return;   // inactive MINRES iteration / empty range
 
   if (tid == 0) {
     failed = 0;
@@ -328,146 +359,159 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   __syncthreads();
-  const uint32_t bbytes = (uint32_t)(rup(n3, 16) * rup(n3, KSTEP) * (int)sizeof(T));
-  if (tid == 0) {
-    const Tab1D &tb = tabs[P[w.x].ltab[l][2]];
-    stage_b(&tma_bar, bm, bsz, tcpool, tb.tcB[FMT == 1][interior][0], bbytes,
-            tb.tcB[FMT == 1][interior][1], bbytes);
-  }
-  {
-    uint4 *zp = reinterpret_cast<uint4 *>(A);
-    const int nzero = cap * (int)sizeof(T) / 16;
-    for (int i = tid; i < nzero; i += 256) zp[i] = make_uint4(0u, 0u, 0u, 0u);
-  }
-  __syncthreads();
-  const int Kp = rup(n3, KSTEP), Np = rup(n3, 16), kch = Kp / T16;
-  // operand: row = line (128), k = i3.  A warp moves 8 lines x 4 planes per
-  // instruction: 32-byte runs in global memory, one 16-byte unit per row in
-  // shared memory.
-  if ((LN & 3) == 0 && ((uintptr_t)X & 15) == 0) {
-    // aligned planes: a lane moves 4 consecutive lines of one plane with a
-    // 16-byte load (a warp: 16 lines x 8 planes per instruction)
-    const int l4 = lane & 3, k8 = lane >> 2;
-    const int nk8 = (n3 + 7) / 8, nitem = 8 * nk8;
-    constexpr int LB = 4;
-    for (int i0 = warp; i0 < nitem; i0 += 8 * LB) {
-      float v[LB][4];
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int it = i0 + u * 8;
-        const int rg = it % 8, kg = it / 8;
-        const int row = rg * 16 + l4 * 4, k = kg * 8 + k8;
-        const bool in = it < nitem && k < n3;
-        if (in && row + 3 < nl) {
-          ld4(X + (long long)k * LN + row, v[u]);
-        } else {
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            v[u][e] = (in && row + e < nl) ? __ldg(X + (long long)k * LN + row + e) : 0.f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int it = i0 + u * 8;
-        const int rg = it % 8, kg = it / 8;
-        const int row = rg * 16 + l4 * 4, k = kg * 8 + k8;
-        if (it < nitem && k < n3)
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (row + e < nl) A[cmp<FMT>(row + e, k, kch)] = Op<FMT>::cvt(v[u][e]);
-      }
-    }
-  } else {
-    const int r8 = lane & 7, k4 = lane >> 3;
-    const int nk4 = (n3 + 3) / 4, nitem = 16 * nk4;
-    constexpr int LB = 8;
-    for (int i0 = warp; i0 < nitem; i0 += 8 * LB) {
-      float v[LB];
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int it = i0 + u * 8;
-        const int rg = it % 16, kg = it / 16;
-        const int row = rg * 8 + r8, k = kg * 4 + k4;
-        v[u] = (it < nitem && row < nl && k < n3) ? __ldg(X + (long long)k * LN + row) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < LB; ++u) {
-        const int it = i0 + u * 8;
-        const int rg = it % 16, kg = it / 16;
-        const int row = rg * 8 + r8, k = kg * 4 + k4;
-        if (it < nitem && row < nl && k < n3) A[cmp<FMT>(row, k, kch)] = Op<FMT>::cvt(v[u]);
-      }
-    }
-  }
-  if (!wait_phase(&tma_bar, 0)) failed = 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
                  "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  asm volatile("fence.proxy.async.shared::cta;");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tslot;
   const int q = warp & 3, half = warp >> 2;
   const int row = q * 32 + lane;
-  // Lambda = c1 D1[a1] + c2 D2[a2] + c3 D3[a3] (+1, times H^{d-2}, for P_A)
-  const float hs = (float)pt.lscale, shf = (float)pt.lshift;
-  const DevPatch &pg = P[w.x];   // component-indexed fields straight from global memory
-  const float c0 = (float)pg.lcf[l][0], c1 = (float)pg.lcf[l][1], c2 = (float)pg.lcf[l][2];
-  const int t0 = pg.ltab[l][0], t1 = pg.ltab[l][1], t2 = pg.ltab[l][2];
-  const float *D0 = fpool + (interior ? tabs[t0].Di : tabs[t0].D);
-  const float *D1 = fpool + (interior ? tabs[t1].Di : tabs[t1].D);
-  const float *D2 = fpool + (interior ? tabs[t2].Di : tabs[t2].D);
-  float lab = 0.f;
-  if (row < nl) {
-    const int line = line0 + row, a2 = line / n1, a1 = line - a2 * n1;
-    lab = c0 * D0[a1] + c1 * D1[a2];
-  }
-  const int nch = Np / 8;
+  int key = -1;            // table of the B operands held in shared memory
+  uint32_t tma_phase = 0;
 
-  for (int m = 0; m < 2; ++m) {
-    if (tid == 0 && !failed) {
-      issue_product<FMT>(tmem, A, bm + m * bsz, 1, Kp, Np);
-      commit(&mbar);
+  for (int wi = w0; wi < w1; ++wi) {
+    const int2 w = work[wi];
+    const DevPatch &pg = P[w.x];   // component-indexed fields straight from global memory
+    const int n1 = interior ? pg.ni[0] : pg.n[0], n2 = interior ? pg.ni[1] : pg.n[1];
+    const int n3 = interior ? pg.ni[2] : pg.n[2];
+    const int LN = n1 * n2, line0 = w.y, nl = min(128, LN - line0);
+    float *X = scr + (interior ? pg.ioff : pg.off) + (long long)l * LN * n3 +
+               (long long)blockIdx.z * rhs_stride + line0;
+    const int t0 = pg.ltab[l][0], t1 = pg.ltab[l][1], t2 = pg.ltab[l][2];
+    const bool reload = t2 != key;
+    const uint32_t bbytes = (uint32_t)(rup(n3, 16) * rup(n3, KSTEP) * (int)sizeof(T));
+    if (reload && tid == 0) {
+      const Tab1D &tb = tabs[t2];
+      stage_b(&tma_bar, bm, bsz, tcpool, tb.tcB[FMT == 1][interior][0], bbytes,
+              tb.tcB[FMT == 1][interior][1], bbytes);
     }
-    if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;");
+    {   // a fresh zero operand per item (no value of the previous item may reach the K padding)
+      uint4 *zp = reinterpret_cast<uint4 *>(A);
+      const int nzero = cap * (int)sizeof(T) / 16;
+      for (int i = tid; i < nzero; i += 256) zp[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     __syncthreads();
+    const int Kp = rup(n3, KSTEP), Np = rup(n3, 16);
+    // operand: row = line (128), k = i3
+    if ((LN & 3) == 0 && ((uintptr_t)X & 15) == 0) {
+      // aligned planes: a lane moves 4 consecutive lines of one plane with a
+      // 16-byte load (a warp: 16 lines x 8 planes per instruction)
+      const int l4 = lane & 3, k8 = lane >> 2;
+      const int nk8 = (n3 + 7) / 8, nitem = 8 * nk8;
+      constexpr int LB = 4;
+      for (int i0 = warp; i0 < nitem; i0 += 8 * LB) {
+        float v[LB][4];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int it = i0 + u * 8;
+          const int rg = it % 8, kg = it / 8;
+          const int r0 = rg * 16 + l4 * 4, k = kg * 8 + k8;
+          const bool in = it < nitem && k < n3;
+          if (in && r0 + 3 < nl) {
+            ld4(X + (long long)k * LN + r0, v[u]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              v[u][e] = (in && r0 + e < nl) ? __ldg(X + (long long)k * LN + r0 + e) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int it = i0 + u * 8;
+          const int rg = it % 8, kg = it / 8;
+          const int r0 = rg * 16 + l4 * 4, k = kg * 8 + k8;
+          if (it < nitem && k < n3)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (r0 + e < nl) A[kslab<FMT>(r0 + e, k, lbo)] = Op<FMT>::cvt(v[u][e]);
+        }
+      }
+    } else {
+      const int r8 = lane & 7, k4 = lane >> 3;
+      const int nk4 = (n3 + 3) / 4, nitem = 16 * nk4;
+      constexpr int LB = 8;
+      for (int i0 = warp; i0 < nitem; i0 += 8 * LB) {
+        float v[LB];
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int it = i0 + u * 8;
+          const int rg = it % 16, kg = it / 16;
+          const int r0 = rg * 8 + r8, k = kg * 4 + k4;
+          v[u] = (it < nitem && r0 < nl && k < n3) ? __ldg(X + (long long)k * LN + r0) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < LB; ++u) {
+          const int it = i0 + u * 8;
+          const int rg = it % 16, kg = it / 16;
+          const int r0 = rg * 8 + r8, k = kg * 4 + k4;
+          if (it < nitem && r0 < nl && k < n3) A[kslab<FMT>(r0, k, lbo)] = Op<FMT>::cvt(v[u]);
+        }
+      }
+    }
+    if (reload) {   // the B operands have landed
+      if (tid == 0 && !wait_phase(&tma_bar, tma_phase)) failed = 1;
+      tma_phase ^= 1u;
+      key = t2;
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
     if (failed) break;
-    for (int c0i = half; c0i < nch; c0i += 4) {
-      uint32_t raw[2][8];
-#pragma unroll
-      for (int u = 0; u < 2; ++u)
-        if (c0i + 2 * u < nch)
-          ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((c0i + 2 * u) * 8), raw[u]);
-      ld_wait();
-      if (row >= nl) continue;
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int j0 = (c0i + 2 * u) * 8;
-        if (j0 >= Np) break;
+    // Lambda = c1 D1[a1] + c2 D2[a2] + c3 D3[a3] (+ shift, times H^{d-2}, for P_A)
+    const float hs = interior ? 1.f : (float)pg.lscale, shf = interior ? 0.f : (float)pg.lshift;
+    const float c0 = (float)pg.lcf[l][0], c1 = (float)pg.lcf[l][1], c2 = (float)pg.lcf[l][2];
+    const float *D0 = fpool + (interior ? tabs[t0].Di : tabs[t0].D);
+    const float *D1 = fpool + (interior ? tabs[t1].Di : tabs[t1].D);
+    const float *D2 = fpool + (interior ? tabs[t2].Di : tabs[t2].D);
+    float lab = 0.f;
+    if (row < nl) {
+      const int ln = line0 + row, a2 = ln / n1, a1 = ln - a2 * n1;
+      lab = hs * (c0 * D0[a1] + c1 * D1[a2] + shf);
+    }
+    const float c2s = hs * c2;
+    const int nch = Np / 8;
+
+    for (int m = 0; m < 2; ++m) {
+      // one thread issues the MMAs and waits for them (two commits per item:
+      // phase parity m); the others wait at the CTA barrier
+      if (tid == 0 && !failed) {
+        issue_product<FMT>(tmem, A, bm + m * bsz, 1, Kp, Np, (uint32_t)lbo * (uint32_t)sizeof(T));
+        commit(&mbar);
+        if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+      }
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      if (failed) break;
+      for (int c0i = half; c0i < nch; c0i += 2) {
+        uint32_t raw[8];
+        ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c0i * 8), raw);
+        ld_wait();
+        if (row >= nl) continue;
+        const int j0 = c0i * 8;
         if (m == 0) {   // scale by Lambda^{-1}, write back as the next operand
           float x[8];
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             const int j = j0 + jj;
-            float lam = lab + c2 * (j < n3 ? D2[j] : 0.f);
-            if (!interior) lam = hs * (lam + shf);
-            x[jj] = (j < n3) ? __fdividef(__uint_as_float(raw[u][jj]), lam) : 0.f;
+            x[jj] = (j < n3) ? __fdividef(__uint_as_float(raw[jj]), lab + c2s * D2[j]) : 0.f;
           }
           if (j0 < Kp) {
             if (FMT == 2) {
-              *reinterpret_cast<float4 *>(&A[cmp<FMT>(row, j0, kch)]) = make_float4(x[0], x[1], x[2], x[3]);
+              *reinterpret_cast<float4 *>(&A[kslab<FMT>(row, j0, lbo)]) = make_float4(x[0], x[1], x[2], x[3]);
               if (j0 + 4 < Kp)
-                *reinterpret_cast<float4 *>(&A[cmp<FMT>(row, j0 + 4, kch)]) =
+                *reinterpret_cast<float4 *>(&A[kslab<FMT>(row, j0 + 4, lbo)]) =
                     make_float4(x[4], x[5], x[6], x[7]);
             } else {
               __nv_bfloat162 h[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(x[2 * e], x[2 * e + 1]);
-              *reinterpret_cast<uint4 *>(&A[cmp<FMT>(row, j0, kch)]) =
+              *reinterpret_cast<uint4 *>(&A[kslab<FMT>(row, j0, lbo)]) =
                   *reinterpret_cast<const uint4 *>(h);
             }
           }
@@ -475,19 +519,22 @@ __global__ void __launch_bounds__(256, 4) k_fd_line(const DevPatch *P, const Tab
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             const int j = j0 + jj;
-            if (j < n3) X[(long long)j * LN + row] = __uint_as_float(raw[u][jj]);
+            if (j < n3) X[(long long)j * LN + row] = __uint_as_float(raw[jj]);
           }
         }
       }
+      asm volatile("fence.proxy.async.shared::cta;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncthreads();
     }
-    asm volatile("fence.proxy.async.shared::cta;");
+    if (failed) break;
+  }
+  if (failed) {   // one more bounded wait for MMAs in flight before freeing TMEM
+    if (tid == 0)
+      for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-  }
-  if (failed) {
-    for (int ph = 0; ph < 2; ++ph) wait_phase(&mbar, (uint32_t)ph);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
   }
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
@@ -511,7 +558,7 @@ struct SlabNeed {
 };
 
 SlabNeed slab_need(const DevPatch &p, int interior, int fmt, int dim) {
-  const int kstep = (fmt == 2) ? 8 : 16, t16 = (fmt == 2) ? 4 : 8;
+  const int kstep = (fmt == 2) ? 8 : 16;
   SlabNeed s{};
   int n[3];
   for (int d = 0; d < 3; ++d) n[d] = interior ? p.ni[d] : p.n[d];
@@ -525,14 +572,14 @@ SlabNeed slab_need(const DevPatch &p, int interior, int fmt, int dim) {
   for (int m = 0; m < 2; ++m) {
     const int na = m ? n[1] : n[0], nb = m ? n[0] : n[1];
     const int Lp = rup(nb * s.nz, 128), Kp = rup(na, kstep), Np = rup(na, 16);
-    s.cap_p = std::max(s.cap_p, (Lp / 8) * (Kp / t16) * 9 * t16);
+    s.cap_p = std::max(s.cap_p, Kp * (Lp + 1));   // K-chunk slabs of Lp + 1 rows
     s.bsz_p = std::max(s.bsz_p, Np * Kp);
     ntile = std::max(ntile, Lp / 128);
     s.tcols_p = std::max(s.tcols_p, tc_cols((Lp / 128) * Np));
   }
   if (s.tcols_p > 512 || ntile > 2) s.ok = false;
   const int Kp3 = rup(n[2], kstep), Np3 = rup(n[2], 16);
-  s.cap_l = 16 * (Kp3 / t16) * 9 * t16;
+  s.cap_l = Kp3 * (128 + 1);
   s.bsz_l = Np3 * Kp3;
   s.tcols_l = tc_cols(Np3);
   return s;
@@ -546,14 +593,46 @@ size_t slab_smem(int cap, int bsz, int tcols, int fmt, int nslot = 2) {
   return std::max(smem, floor_smem);
 }
 
+// Bounds of nb contiguous ranges of the items with about equal total cost
+// (empty ranges allowed).
+std::vector<int> balanced_ranges(const std::vector<long long> &cost, int nb) {
+  long long total = 0;
+  for (long long c : cost) total += c;
+  std::vector<int> b(nb + 1, (int)cost.size());
+  b[0] = 0;
+  long long acc = 0;
+  int k = 1;
+  for (int i = 0; i < (int)cost.size() && k < nb; ++i) {
+    acc += cost[i];
+    while (k < nb && acc * nb >= total * (long long)k) b[k++] = i + 1;
+  }
+  return b;
+}
+
+// CTAs per (component, right-hand side): at least the resident CTAs of the
+// whole GPU shared over the components, and about two items per CTA, so that
+// a CTA's setup (tensor memory, barriers, B operands) is shared by a few
+// items while CTAs that finish early are replaced by waiting ones (a single
+// wave of long ranges measured 35% slower with one right-hand side).
+template <typename K>
+afi_status persistent_grid(afi_ctx *c, K kern, size_t smem, int nitems, int *grid) {
+  int occ = 0;
+  AFI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem));
+  const int wave = c->nsm * std::max(occ, 1) / std::max(c->dim, 1);
+  *grid = std::max(1, std::min(nitems, std::max(wave, (nitems + 1) / 2)));
+  return AFI_OK;
+}
+
 }  // namespace
 
 // Decide which of the given patches the slab path takes (the rest stay with
-// the SIMT kernel) and build the pass work lists.
+// the SIMT kernel) and build the pass work lists and the persistent CTAs'
+// ranges of them.
 afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> &cand,
                       std::vector<int> &rest, TcSplit &sp, int dyn_max) {
   std::vector<int4> pw;
   std::vector<int2> lw;
+  std::vector<long long> pcost, lcost;
   int cap_p = 0, bsz_p = 0, tcols_p = 32, cap_l = 0, bsz_l = 0, tcols_l = 32, nslot_p = 1;
   for (int k : cand) {
     const DevPatch &p = c->hp[k];
@@ -573,8 +652,14 @@ afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> 
     nslot_p = nsp;
     const int n1 = interior ? p.ni[0] : p.n[0], n2 = interior ? p.ni[1] : p.n[1];
     const int n3 = interior ? p.ni[2] : p.n[2];
-    for (int z = 0; z < n3; z += s.nz) pw.push_back(make_int4(k, z, std::min(s.nz, n3 - z), 0));
-    for (int ln = 0; ln < n1 * n2; ln += 128) lw.push_back(make_int2(k, ln));
+    for (int z = 0; z < n3; z += s.nz) {
+      pw.push_back(make_int4(k, z, std::min(s.nz, n3 - z), 0));
+      pcost.push_back((long long)n1 * n2 * std::min(s.nz, n3 - z));
+    }
+    for (int ln = 0; ln < n1 * n2; ln += 128) {
+      lw.push_back(make_int2(k, ln));
+      lcost.push_back((long long)std::min(128, n1 * n2 - ln) * n3);
+    }
   }
   sp.nplane = (int)pw.size();
   sp.nline = (int)lw.size();
@@ -591,6 +676,18 @@ afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> 
     AFI_CUDA(cudaMemcpy(sp.d_plane, pw.data(), pw.size() * sizeof(int4), cudaMemcpyHostToDevice));
     AFI_TRY(dalloc(c, (void **)&sp.d_line, lw.size() * sizeof(int2)));
     AFI_CUDA(cudaMemcpy(sp.d_line, lw.data(), lw.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    if (fmt == 2) {
+      AFI_TRY(persistent_grid(c, k_fd_plane<2, 0>, sp.smem_p, sp.nplane, &sp.pgrid));
+      AFI_TRY(persistent_grid(c, k_fd_line<2>, sp.smem_l, sp.nline, &sp.lgrid));
+    } else {
+      AFI_TRY(persistent_grid(c, k_fd_plane<1, 0>, sp.smem_p, sp.nplane, &sp.pgrid));
+      AFI_TRY(persistent_grid(c, k_fd_line<1>, sp.smem_l, sp.nline, &sp.lgrid));
+    }
+    const std::vector<int> pb = balanced_ranges(pcost, sp.pgrid), lb = balanced_ranges(lcost, sp.lgrid);
+    AFI_TRY(dalloc(c, (void **)&sp.d_pbounds, pb.size() * sizeof(int)));
+    AFI_CUDA(cudaMemcpy(sp.d_pbounds, pb.data(), pb.size() * sizeof(int), cudaMemcpyHostToDevice));
+    AFI_TRY(dalloc(c, (void **)&sp.d_lbounds, lb.size() * sizeof(int)));
+    AFI_CUDA(cudaMemcpy(sp.d_lbounds, lb.data(), lb.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
   return AFI_OK;
 }
@@ -629,22 +726,23 @@ afi_status slab_run(afi_ctx *c, int interior, int fmt, const TcSplit &sp, const 
     const int nb = std::min(chunk, nrhs - j);
     const double *rj = r + (long long)j * stride;
     double *sj = s + (long long)j * stride;
-    const dim3 gp(sp.nplane, c->dim, nb), gl(sp.nline, c->dim, nb);
+    const dim3 gp(sp.pgrid, c->dim, nb), gl(sp.lgrid, c->dim, nb);
+    const int *pb = sp.d_pbounds, *lb = sp.d_lbounds;
     if (fmt == 2) {
-      launch(k_fd_plane<2, 0>, gp, 256, sp.smem_p, st, P, tabs, pw, interior, rj, scr, sj, stride,
+      launch(k_fd_plane<2, 0>, gp, 256, sp.smem_p, st, P, tabs, pw, pb, interior, rj, scr, sj, stride,
              sp.cap_p, sp.bsz_p, sp.tcols_p, c->gate, c->dflag + 1, (const unsigned char *)c->tcpool);
-      launch(k_fd_line<2>, gl, 256, sp.smem_l, st, P, tabs, (const float *)c->fpool, lw, interior, scr,
-             stride, sp.cap_l, sp.bsz_l, sp.tcols_l, c->gate, c->dflag + 1,
+      launch(k_fd_line<2>, gl, 256, sp.smem_l, st, P, tabs, (const float *)c->fpool, lw, lb, interior,
+             scr, stride, sp.cap_l, sp.bsz_l, sp.tcols_l, c->gate, c->dflag + 1,
              (const unsigned char *)c->tcpool);
-      launch(k_fd_plane<2, 1>, gp, 256, sp.smem_p, st, P, tabs, pw, interior, rj, scr, sj, stride,
+      launch(k_fd_plane<2, 1>, gp, 256, sp.smem_p, st, P, tabs, pw, pb, interior, rj, scr, sj, stride,
              sp.cap_p, sp.bsz_p, sp.tcols_p, c->gate, c->dflag + 1, (const unsigned char *)c->tcpool);
     } else {
-      launch(k_fd_plane<1, 0>, gp, 256, sp.smem_p, st, P, tabs, pw, interior, rj, scr, sj, stride,
+      launch(k_fd_plane<1, 0>, gp, 256, sp.smem_p, st, P, tabs, pw, pb, interior, rj, scr, sj, stride,
              sp.cap_p, sp.bsz_p, sp.tcols_p, c->gate, c->dflag + 1, (const unsigned char *)c->tcpool);
-      launch(k_fd_line<1>, gl, 256, sp.smem_l, st, P, tabs, (const float *)c->fpool, lw, interior, scr,
-             stride, sp.cap_l, sp.bsz_l, sp.tcols_l, c->gate, c->dflag + 1,
+      launch(k_fd_line<1>, gl, 256, sp.smem_l, st, P, tabs, (const float *)c->fpool, lw, lb, interior,
+             scr, stride, sp.cap_l, sp.bsz_l, sp.tcols_l, c->gate, c->dflag + 1,
              (const unsigned char *)c->tcpool);
-      launch(k_fd_plane<1, 1>, gp, 256, sp.smem_p, st, P, tabs, pw, interior, rj, scr, sj, stride,
+      launch(k_fd_plane<1, 1>, gp, 256, sp.smem_p, st, P, tabs, pw, pb, interior, rj, scr, sj, stride,
              sp.cap_p, sp.bsz_p, sp.tcols_p, c->gate, c->dflag + 1, (const unsigned char *)c->tcpool);
     }
     AFI_LAUNCH_CHECK();

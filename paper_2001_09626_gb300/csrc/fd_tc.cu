@@ -55,14 +55,6 @@ __host__ __device__ __forceinline__ int bslot(unsigned packed, int m) {
   return (int)((packed >> (4 * m)) & 15u);
 }
 
-// element offset of (row, k) in the tensor operand: K chunk k / T16 of
-// lbo = (Lp + 1) T16 elements, rows T16 elements apart
-template <int FMT>
-__device__ __forceinline__ int kslab(int row, int k, int lbo) {
-  constexpr int T16 = tc::Op<FMT>::T16;
-  return (k / T16) * lbo + row * T16 + (k % T16);
-}
-
 // Epilogue of one mode product: D[line][j] from tensor memory to registers,
 // then (KIND 0) into the next operand with the axes rotated, in place;
 // (KIND 1) the same after the scaling by Lambda^{-1}; (KIND 2) as FP64 into
@@ -406,7 +398,7 @@ static afi_status build_split_thr(afi_ctx *c, int interior, int fmt, size_t thr,
 }
 
 static void free_split(TcSplit &sp) {
-  void *p[] = {sp.d_tc, sp.d_simt, sp.d_plane, sp.d_line};
+  void *p[] = {sp.d_tc, sp.d_simt, sp.d_plane, sp.d_line, sp.d_pbounds, sp.d_lbounds};
   for (void *q : p)
     if (q) cudaFree(q);
   sp = TcSplit{};

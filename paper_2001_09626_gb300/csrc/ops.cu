@@ -184,7 +184,8 @@ __device__ __forceinline__ RigidNZ rigid_nz(int comp, const double *X, int dim) 
 
 constexpr int kCounters = 3072;  // block tickets of the last-block reductions, in c->small
 constexpr int kGtBlocks = 4;    // blocks per patch for the row-list reduction
-constexpr int kRtChunks = 4;    // blocks per (patch, component) for R^T v
+constexpr int kRtChunks = 16;   // blocks per (patch, component) for R^T v (partials:
+                                 // dim * 16 * 3 <= the 320 per patch of the P_u slice)
 
 // After each block has written its partials: true (in every thread) in the
 // block that finishes last, which then combines all partials; it resets the

@@ -147,16 +147,16 @@ __device__ __forceinline__ int cm(int row, int k, int Kp) {
   return (((row >> 3) * (Kp / T16) + k / T16) * 8 + (row & 7)) * T16 + (k % T16);
 }
 
-// The tensor operand uses the same core matrices, but K-adjacent ones sit
-// kLBO = 144 bytes apart (a 16-byte gap): a warp writing one row across its
-// K chunks then touches distinct shared-memory banks.  kch = K chunks of 16
-// bytes per row group.
-constexpr int kLBO = 144;
-
+// The tensor operands of the FD kernels store each 16-byte K chunk of all
+// their rows as one slab: rows 16 bytes apart (8-row groups 128 bytes apart)
+// and chunks lbo = (Lp + 1) x 16 bytes apart, Lp = rows padded to the
+// 128-row tile.  An element's offset is then linear in its row, and the
+// extra 16 bytes per slab put a warp writing one row across its K chunks on
+// distinct shared-memory banks.  Element offset of (row, k), lbo in elements:
 template <int FMT>
-__device__ __forceinline__ int cmp(int row, int k, int kch) {
+__device__ __forceinline__ int kslab(int row, int k, int lbo) {
   constexpr int T16 = Op<FMT>::T16;
-  return T16 * (9 * ((row >> 3) * kch + k / T16) + (row & 7)) + (k % T16);
+  return (k / T16) * lbo + row * T16 + (k % T16);
 }
 
 }  // namespace tc
