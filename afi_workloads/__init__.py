@@ -43,6 +43,10 @@ class Problem:
     dirichlet_face: np.ndarray      # [npatch, 2*dim] uint8
     global_index: list = field(default_factory=list)  # per patch int64 node ids
     grid: tuple = ()                # patches per direction (structured layouts)
+    # nested non-conforming interfaces (Section 2): (coarse patch, its face,
+    # fine patch, its face), face = 2*direction + side; the fine face's knot
+    # vectors refine the coarse face's in the same tangential order
+    nested: list = field(default_factory=list)
 
     @property
     def npatch(self) -> int:
@@ -182,6 +186,50 @@ def twisted_box(grid=(8, 8, 4), p=4, nel=48, name=None):
     return _structured(name or f"twist_p{p}_nel{nel}", 3, grid, nel_cols, p, geom)
 
 
+def nested_box(dim=3, nels=(4, 8, 16), p=2, name=None) -> Problem:
+    """The paper's non-conforming test layout (Section 6): the box
+    (0,1) x (0,len(nels)) [x (0,1)] split along direction 2 into unit patches
+    with nels[k] elements per direction in patch k, identity-mapped (the
+    control points are the Greville abscissae, so each fine interface net is
+    the knot-inserted coarse one).  Dirichlet conditions on the whole outer
+    boundary; consecutive patches meet on a nested interface when their
+    element counts divide one another.  Node ids are per patch (no node is
+    shared), so body-force coefficient fields are per patch."""
+    npatch = len(nels)
+    degree = np.full(npatch, p, dtype=np.int32)
+    nel = np.zeros((npatch, dim), dtype=np.int32)
+    ctrl, gidx, nested = [], [], []
+    dface = np.zeros((npatch, 2 * dim), dtype=np.uint8)
+    base = 0
+    for k, ne in enumerate(nels):
+        nel[k, :] = ne
+        params = [_patch_params(0.0, 1.0, ne, p) for _ in range(dim)]
+        params[1] = params[1] + k
+        mesh = np.meshgrid(*params[::-1], indexing="ij")
+        ctrl.append(np.ascontiguousarray(np.stack(mesh[::-1], axis=-1), dtype=np.float64))
+        n = ne + p
+        gidx.append(base + np.arange(n ** dim, dtype=np.int64).reshape((n,) * dim))
+        base += n ** dim
+        for l in range(dim):
+            for side in range(2):
+                outer = l != 1 or (side == 0 and k == 0) or (side == 1 and k == npatch - 1)
+                dface[k, 2 * l + side] = 1 if outer else 0
+    for k in range(npatch - 1):
+        a, b = nels[k], nels[k + 1]
+        if a == b:
+            continue
+        if b % a == 0:
+            nested.append((k, 3, k + 1, 2))
+        elif a % b == 0:
+            nested.append((k + 1, 2, k, 3))
+        else:
+            raise ValueError("consecutive element counts must divide one another")
+    lam = np.tile(np.array((STEEL_LAMBDA, STEEL_MU), dtype=np.float64), (npatch, 1))
+    return Problem(name=name or f"nested{dim}d_p{p}_" + "_".join(map(str, nels)), dim=dim,
+                   degree=degree, nel=nel, ctrl=ctrl, lame=lam, dirichlet_face=dface,
+                   global_index=gidx, grid=(1, npatch) + (1,) * (dim - 2), nested=nested)
+
+
 def with_neumann(prob: Problem, faces, name=None) -> Problem:
     """Copy of a structured problem whose outer faces `faces` (parametric face
     indices f = 2*l + side: direction l, side 0 = lower, 1 = upper) carry the
@@ -249,6 +297,12 @@ def config(name: str, seed: int = 0) -> Problem:
         return twisted_box((2, 2, 2), 4, 48, name=name)
     if name == "C1-small":
         return unit_box(2, (2, 2), 2, 3, name=name)
+    if name == "NC-small":   # nested interfaces, 2D, oracle-sized
+        return nested_box(2, (2, 4, 8), 2, name=name)
+    if name == "NC3-small":  # nested interfaces, 3D, oracle-sized
+        return nested_box(3, (1, 2, 4), 2, name=name)
+    if name == "NC3":        # the paper's non-conforming test (4, 8, 16 elements), p = 2
+        return nested_box(3, (4, 8, 16), 2, name=name)
     raise KeyError(name)
 
 

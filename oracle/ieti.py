@@ -9,6 +9,15 @@ Readings where the paper is silent (each listed in the design notes):
     the Dirichlet boundary gets one row e_{c_j} per copy; any other node gets
     the star rows u_{c_1} - u_{c_j}, j = 2..m.  Rows are component-major, then
     nodes ordered by their first copy.
+  * Nested non-conforming interfaces (Section 2; Section 6, non-conforming
+    test): a face whose knot vectors refine the neighbouring patch's.  Its
+    points off the Dirichlet boundary are not matched by coordinates; instead
+    every such fine point f and component gets the row
+    u_f - sum_c W[f, c] u_c over the coarse face points c off the Dirichlet
+    boundary (W = the tensor product of the refinement matrices).  These rows
+    follow all the node rows: faces by (fine patch, fine face), then
+    component, then fine point.  The edges of a nested face must lie on the
+    Dirichlet boundary.
   * lambda_0 = G (G^T G)^{-1} R^T f (minimum-norm choice of "such that").
   * H^(k) = diagonal of the bounding box of the patch control points.
   * P_A = P_A^inex (Section 5.2, plain parametric variant), P_S = the
@@ -23,7 +32,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 from scipy.spatial import cKDTree
 
-from . import assembly, fd
+from . import assembly, fd, nested
 from .minres import minres
 
 
@@ -43,6 +52,12 @@ class AFIETI:
         for k in range(self.np):
             self.off[k + 1] = self.off[k] + d * self.N[k]
         self.ndof = int(self.off[-1])
+        # nested faces: (coarse patch, face, fine patch, face, fine points,
+        # coarse points, weights), ordered by (fine patch, fine face)
+        self.nested_faces = []
+        for (kc, fc, kf, ff) in sorted(getattr(prob, "nested", []), key=lambda t: (t[2], t[3])):
+            pf, pc, W = nested.face_map(prob, kc, fc, kf, ff)
+            self.nested_faces.append((kc, fc, kf, ff, pf, pc, W))
         self._connectivity()
         self._constraints()
         self._rigid()
@@ -58,14 +73,29 @@ class AFIETI:
             i //= n
         return out
 
+    def _on_dirichlet(self, k, i):
+        im = self._multi(k, i)
+        return any(self.prob.dirichlet_face[k, f] and _on_face(im, self.geo[k].ns, f // 2, f % 2)
+                   for f in range(2 * self.dim))
+
     def _connectivity(self):
         """Group shell control points of all patches into geometric nodes by
-        coordinate matching (conforming, watertight interfaces, Section 2.2)."""
-        keys, pts = [], []
+        coordinate matching (conforming, watertight interfaces, Section 2.2).
+        Points of nested faces off the Dirichlet boundary stay single."""
+        apart = set()
+        for (kc, fc, kf, ff, pf, pc, W) in self.nested_faces:
+            for k, pts_ in ((kc, pc), (kf, pf)):
+                for i in pts_:
+                    if not self._on_dirichlet(k, i):
+                        apart.add((k, i))
+        keys, pts, single = [], [], []
         for k, g in enumerate(self.geo):
             for i in range(self.N[k]):
                 im = self._multi(k, i)
                 if any(im[l] in (0, g.ns[l] - 1) for l in range(self.dim)):
+                    if (k, i) in apart:
+                        single.append([(k, i)])
+                        continue
                     keys.append((k, i))
                     pts.append(g.X[i])
         pts = np.array(pts)
@@ -85,7 +115,7 @@ class AFIETI:
         groups = {}
         for a in range(len(keys)):
             groups.setdefault(find(a), []).append(keys[a])
-        nodes = [sorted(v) for v in groups.values()]
+        nodes = [sorted(v) for v in groups.values()] + single
         nodes.sort(key=lambda c: c[0])
         self.nodes = nodes
         self.dirichlet = []
@@ -120,6 +150,21 @@ class AFIETI:
                         vals += [1.0, -1.0]
                         ids.append(r); r += 1
                 self.node_rows.append((c, n, ids))
+        # nested faces: u_f - sum_c W[f, c] u_c per free fine point
+        self.nested_rows = []    # (component, fine patch, fine face, list of row ids)
+        for (kc, fc, kf, ff, pf, pc, W) in self.nested_faces:
+            cfree = [j for j, i in enumerate(pc) if not self._on_dirichlet(kc, i)]
+            for c in range(self.dim):
+                ids = []
+                for a, i in enumerate(pf):
+                    if self._on_dirichlet(kf, i):
+                        continue
+                    rows.append(r); cols.append(self.dof(kf, c, i)); vals.append(1.0)
+                    for j in cfree:
+                        if W[a, j] != 0.0:
+                            rows.append(r); cols.append(self.dof(kc, c, pc[j])); vals.append(-W[a, j])
+                    ids.append(r); r += 1
+                self.nested_rows.append((c, kf, ff, ids))
         self.nc = r
         self.B = sp.csr_matrix((vals, (rows, cols)), shape=(self.nc, self.ndof))
         shell = np.zeros(self.ndof, dtype=bool)
@@ -375,26 +420,39 @@ class AFIETI:
 
     # ------------------------------------------------------- direct reference
     def conforming_basis(self):
-        """Z: torn copies of every free (non-Dirichlet) global node/component."""
-        rows, cols = [], []
+        """Z: torn copies of every free (non-Dirichlet) global node/component;
+        on a nested face the free fine points are not free: they follow the
+        free coarse points with the weights W (the knot-insertion relation)."""
+        rows, cols, vals = [], [], []
         col = 0
         shell_set = {}
         for n, copies in enumerate(self.nodes):
             for (k, i) in copies:
                 shell_set[(k, i)] = n
+        follows, fine_dep = {}, set()
+        for (kc, fc, kf, ff, pf, pc, W) in self.nested_faces:
+            for a, i in enumerate(pf):
+                if self._on_dirichlet(kf, i):
+                    continue
+                fine_dep.add((kf, i))
+                for j, ic in enumerate(pc):
+                    if W[a, j] != 0.0 and not self._on_dirichlet(kc, ic):
+                        follows.setdefault((kc, ic), []).append((kf, i, W[a, j]))
         for c in range(self.dim):
             for n, copies in enumerate(self.nodes):
-                if self.dirichlet[n]:
+                if self.dirichlet[n] or (len(copies) == 1 and copies[0] in fine_dep):
                     continue
                 for (k, i) in copies:
-                    rows.append(self.dof(k, c, i)); cols.append(col)
+                    rows.append(self.dof(k, c, i)); cols.append(col); vals.append(1.0)
+                    for (kf, i2, w) in follows.get((k, i), []):
+                        rows.append(self.dof(kf, c, i2)); cols.append(col); vals.append(w)
                 col += 1
             for k in range(self.np):
                 for i in range(self.N[k]):
                     if (k, i) not in shell_set:
-                        rows.append(self.dof(k, c, i)); cols.append(col)
+                        rows.append(self.dof(k, c, i)); cols.append(col); vals.append(1.0)
                         col += 1
-        return sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(self.ndof, col))
+        return sp.csr_matrix((vals, (rows, cols)), shape=(self.ndof, col))
 
     def direct_solve(self, f):
         """The conforming Galerkin solution of eq. 3.2 (unique by Section 4)

@@ -40,6 +40,9 @@ def mult_blocks(orc):
         k = orc.nodes[n][0][0]
         for r in ids:
             first[r] = (c, k)
+    for (c, kf, ff, ids) in getattr(orc, "nested_rows", []):
+        for r in ids:
+            first[r] = ("nested", c, kf, ff)
     out, start = [], 0
     for r in range(1, orc.nc + 1):
         if r == orc.nc or first[r] != first[start]:
