@@ -71,8 +71,18 @@ typedef struct afi_ctx afi_ctx;   /* opaque, owned by the library */
  *   ctrl           control points of all patches concatenated, each patch
  *                  [i3][i2][i1][dim] (i1 fastest); the geometry map is the
  *                  isoparametric spline map of Section 2.2.  Shared interface
- *                  control points must coincide (conforming patches); they
- *                  are matched by coordinates (relative tolerance 1e-10)
+ *                  control points of conforming faces must coincide; they
+ *                  are matched by coordinates (relative tolerance 1e-10).
+ *                  A face whose knot vectors refine the neighbour's (nested
+ *                  non-conforming interface, Section 2) is found by its
+ *                  corners: same corners in the same tangential order, one
+ *                  degree, element counts that divide, the fine control net
+ *                  equal to the refined coarse net, and face edges on the
+ *                  Dirichlet boundary.  Each of its fine coefficients off
+ *                  the Dirichlet boundary gets the row
+ *                  u_fine - sum W u_coarse (W the knot-insertion weights);
+ *                  these rows follow the node rows, by (fine patch, fine
+ *                  face), then component, then fine point
  *   lame[2k+0,1]   (lambda_k, mu_k) of patch k (eq. 3.1)
  *   dirichlet_face[k*2*dim + 2*l + side]  1 if the face eta_l = side of
  *                  patch k carries the homogeneous Dirichlet condition      */
@@ -232,8 +242,9 @@ typedef enum {
  * assembly of every patch stiffness A^(k) by Gauss quadrature with p+1
  * points per element and direction).  Runs on the current device, returns
  * after the work is complete.  *out receives a new context on success.
- * Errors: AFI_EINVAL (bad sizes, non-conforming interfaces, det J <= 0),
- * AFI_ESINGULAR (G^T G not positive definite), AFI_ENOMEM, AFI_ECUDA. */
+ * Errors: AFI_EINVAL (bad sizes, faces that neither match nor nest as
+ * described above, det J <= 0), AFI_ESINGULAR (G^T G or the B B^T block of
+ * a nested face not positive definite), AFI_ENOMEM, AFI_ECUDA. */
 afi_status af_ieti_setup(const afi_problem *prob, const afi_options *opt, afi_ctx **out);
 
 /* Algorithm 1 (steps 2-4) on every (patch, component) block:

@@ -3,9 +3,12 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <array>
 #include <atomic>
 #include <cstdint>
+#include <set>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/afieti.h"
@@ -165,6 +168,7 @@ struct afi_ctx {
   int dim = 0, npatch = 0, nm = 0;   // nm = rigid modes per patch
   int device = 0;
   long n_dof = 0, n_c = 0, n_int = 0;
+  long n_c0 = 0;                     // rows of the conforming nodes (the first n_c0 of n_c)
   afi_options opt{};
   double t_setup_ms = 0.0;
   double t_fd_setup_ms = 0.0;        // local-solver part of the setup (Algorithm 1 step 1)
@@ -217,6 +221,22 @@ struct afi_ctx {
   double2 *prow_coef = nullptr;  // rotation coefficients (v1, v2) of each entry
   int2 *row_cp = nullptr;        // per row: (patch*4 + component) of copy A, of copy B or -1
   double4_32a *row_cv = nullptr;     // per row: (v1, v2) of copy A, (v1, v2) of copy B
+  // nested non-conforming faces (rows n_c0 .. n_c - 1): row r is
+  // u_fine - sum W u_coarse; entries CSR, the fine dof first
+  long n_nest = 0, n_nd = 0;         // nested rows, dofs they touch
+  int n_nblk = 0;                    // (face, component) blocks of B B^T
+  int *nest_ptr = nullptr, *nest_ent = nullptr;   // row CSR: entry dofs
+  double *nest_w = nullptr;                       // entry weights (+1, -W)
+  int4 *nest_eki = nullptr;          // per entry: (patch, component, local index, side)
+  int *nd_dof = nullptr, *nd_ptr = nullptr, *nd_ent = nullptr;   // transposed CSR
+  double *nd_w = nullptr;
+  int *nblk_ptr = nullptr;           // block row ranges (nested-local rows)
+  long long *nblk_off = nullptr;     // offsets of the blocks' dense inverses in nest_binv
+  double *nest_binv = nullptr;       // (B B^T)^{-1} of each block, row-major
+  int2 *nest_gk = nullptr;           // per row: (fine patch, coarse patch)
+  double *nest_gc = nullptr;         // per row: G coefficients [2][nm] (fine, coarse)
+  int *pn_ptr = nullptr, *pn_ent = nullptr;   // per patch: nested rows touching it (row*2 + side)
+  double *nest_tmp = nullptr;        // n_nest scratch of the Schur-type block
   int *pair_ptr = nullptr;       // G^T G off-diagonal pair blocks
   int2 *pair_kk = nullptr;       // (k, k')
   int4 *pair_ent = nullptr;      // (dofA, dofB, sign product, unused)
@@ -300,6 +320,18 @@ afi_status op_dense_inv(afi_ctx *c, const double *g, double *y, cudaStream_t s);
 afi_status op_G(afi_ctx *c, const double *y, double *out, bool subtract, cudaStream_t s);
 afi_status op_R_sub(afi_ctx *c, const double *y, double *v, cudaStream_t s);
 afi_status rigid_tables(afi_ctx *c);
+// nested non-conforming faces (nested.cu: detection, rows, blocks; ops.cu:
+// the G coefficients of the rows)
+struct NestedFace {
+  int kc, fc, kf, ff;            // coarse patch and face, fine patch and face (face = 2 l + side)
+  std::vector<int> pc, pf;       // face points (local indices, increasing)
+  std::vector<double> W;         // [pf.size()][pc.size()]: fine = W coarse
+};
+afi_status nested_detect(afi_ctx *c, const afi_problem *prob, double quant,
+                         std::vector<NestedFace> &faces, std::set<std::pair<int, int>> &apart);
+afi_status nested_build(afi_ctx *c, const afi_problem *prob, const std::vector<NestedFace> &faces);
+afi_status nested_gcoef(afi_ctx *c);
+afi_status nested_gtg(afi_ctx *c);
 afi_status op_PS(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status op_precond(afi_ctx *c, const double *x, double *y, cudaStream_t s);
 afi_status op_saddle(afi_ctx *c, const double *x, double *y, cudaStream_t s);

@@ -57,6 +57,11 @@ __device__ __forceinline__ void block_sum_multi(double *vals, int nv, double *sh
   __syncthreads();
 }
 
+// the nested-face rows (defined below, with their kernels)
+static void nest_B(afi_ctx *c, const double *x, double *yr, double alpha, int acc, cudaStream_t s);
+static void nest_Bt(afi_ctx *c, const double *xr, double *y, double alpha, int acc, cudaStream_t s);
+static void nest_blockinv(afi_ctx *c, const double *xr, double *yr, cudaStream_t s);
+
 // ------------------------------------------------------------------ jumps
 __global__ void k_B(const int2 *rc, long n_c, const double *x, double *y, double alpha, int acc, const double *gate) {
   if (gate && *gate == 0.0) return;   // inactive MINRES iteration
@@ -136,7 +141,10 @@ __global__ void k_B_inv(const int2 *rc, const int2 *grp, long n_c, const double 
 
 afi_status op_B(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->n_c == 0) return AFI_OK;
-  launch(k_B, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->row_copy, c->n_c, x, y, 1.0, 0, (const double *)c->gate);
+  if (c->n_c0)
+    launch(k_B, (unsigned)((c->n_c0 + 255) / 256), 256, 0, s, c->row_copy, c->n_c0, x, y, 1.0, 0,
+           (const double *)c->gate);
+  if (c->n_nest) nest_B(c, x, y + c->n_c0, 1.0, 0, s);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -144,9 +152,10 @@ afi_status op_B(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
 static afi_status op_Bt_scaled(afi_ctx *c, const double *x, double *y, double alpha, bool acc,
                                bool zero_first, cudaStream_t s) {
   if (zero_first) AFI_CUDA(cudaMemsetAsync(y, 0, c->n_dof * sizeof(double), s));
-  if (c->n_shell == 0) return AFI_OK;
-  launch(k_Bt, (unsigned)((c->n_shell + 255) / 256), 256, 0, s, c->shell_dof, c->bt_ptr, c->bt_ent,
-                                                            c->n_shell, x, y, alpha, acc ? 1 : 0, (const double *)c->gate);
+  if (c->n_shell)
+    launch(k_Bt, (unsigned)((c->n_shell + 255) / 256), 256, 0, s, c->shell_dof, c->bt_ptr, c->bt_ent,
+           c->n_shell, x, y, alpha, acc ? 1 : 0, (const double *)c->gate);
+  if (c->n_nest) nest_Bt(c, x + c->n_c0, y, alpha, acc ? 1 : 0, s);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -158,7 +167,10 @@ afi_status op_Bt(afi_ctx *c, const double *x, double *y, bool accumulate, bool z
 
 afi_status op_BBt_inv(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->n_c == 0) return AFI_OK;
-  launch(k_BBt_inv, (unsigned)((c->n_c + 255) / 256), 256, 0, s, c->row_grp, c->n_c, x, y, (const double *)c->gate);
+  if (c->n_c0)
+    launch(k_BBt_inv, (unsigned)((c->n_c0 + 255) / 256), 256, 0, s, c->row_grp, c->n_c0, x, y,
+           (const double *)c->gate);
+  if (c->n_nest) nest_blockinv(c, x + c->n_c0, y + c->n_c0, s);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -317,6 +329,132 @@ __global__ void k_Rsub(const DevPatch *P, const double *ctrl, const double *src,
   dst[at] = src[at] - sub;
 }
 
+// ------------------------------------------------ nested faces (rows n_c0..)
+// The rows of nested non-conforming faces (nested.cu): row r is
+// u_fine - sum W u_coarse, CSR entries (dof, weight); xr / yr point at the
+// first nested row of a multiplier vector.
+
+// G coefficients of every nested row (setup): per side (fine, coarse) the
+// row's products with the patch's rigid modes, sum over the entries of
+// weight x R(dof, mode).
+__global__ void k_nest_gcoef(const DevPatch *P, const double *ctrl, const int *ptr, const double *w,
+                             const int4 *eki, int nr, int dim, int nm, double *gc) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  double g[2][6] = {{0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};
+  for (int e = ptr[r]; e < ptr[r + 1]; ++e) {
+    const int4 q = eki[e];
+    const RigidNZ rz = rigid_nz(q.y, ctrl + P[q.x].xoff + (long long)q.z * dim, dim);
+    const double we = w[e];
+    g[q.w][q.y] += we;
+    g[q.w][rz.m1] += we * rz.v1;
+    if (dim == 3) g[q.w][rz.m2] += we * rz.v2;
+  }
+  for (int sd = 0; sd < 2; ++sd)
+    for (int a = 0; a < nm; ++a) gc[((long long)r * 2 + sd) * nm + a] = g[sd][a];
+}
+
+// yr[r] (= or += alpha *) sum over the row's entries of weight * x[dof]
+__global__ void k_nest_B(const int *ptr, const int *ent, const double *w, long nr, const double *x,
+                         double *yr, double alpha, int acc, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
+  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  double v = 0.0;
+  for (int e = ptr[r]; e < ptr[r + 1]; ++e) v += w[e] * x[ent[e]];
+  yr[r] = acc ? yr[r] + alpha * v : alpha * v;
+}
+
+// y[dof] (= or += alpha *) sum over the nested rows touching the dof of
+// weight * xr[row], for the dofs the nested rows touch
+__global__ void k_nest_Bt(const int *dofs, const int *ptr, const int *ent, const double *w, long nd,
+                          const double *xr, double *y, double alpha, int acc, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
+  const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  double v = 0.0;
+  for (int e = ptr[i]; e < ptr[i + 1]; ++e) v += w[e] * xr[ent[e]];
+  const int d = dofs[i];
+  y[d] = acc ? y[d] + alpha * v : alpha * v;
+}
+
+// yr = blockdiag((B B^T)^{-1}) xr over the (face, component) blocks: one CTA
+// per block, one warp per row of the block's dense inverse
+__global__ void k_nest_blockinv(const int *bptr, const long long *boff, const double *binv,
+                                const double *xr, double *yr, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
+  const int b = blockIdx.x, r0 = bptr[b], m = bptr[b + 1] - r0;
+  const double *M = binv + boff[b];
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x >> 5; i < m; i += nw) {
+    double v = 0.0;
+    for (int j = lane; j < m; j += 32) v += M[(long long)i * m + j] * xr[r0 + j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) yr[r0 + i] = v;
+  }
+}
+
+// outr[r] = (src ? srcr[r] - : ) (G y)[row r]
+__global__ void k_nest_G(const int2 *gk, const double *gc, long nr, int nm, const double *y,
+                         double *outr, const double *srcr, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
+  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const int2 k = gk[r];
+  const double *g = gc + r * 2 * nm;
+  double v = 0.0;
+  for (int a = 0; a < nm; ++a) v += g[a] * y[k.x * nm + a] + g[nm + a] * y[k.y * nm + a];
+  outr[r] = srcr ? srcr[r] - v : v;
+}
+
+// g[k nm + a] += sum over the nested rows touching patch k of their
+// coefficient of mode a times xr[row]: one CTA per patch, fixed order
+template <int NM>
+__global__ void __launch_bounds__(256) k_nest_Gt(const int *pptr, const int *pent, const double *gc,
+                                                 const double *xr, double *g, const double *gate) {
+  if (gate && *gate == 0.0) return;   // inactive MINRES iteration
+  __shared__ double sh[8 * NM];
+  const int k = blockIdx.x;
+  double acc[NM];
+#pragma unroll
+  for (int a = 0; a < NM; ++a) acc[a] = 0.0;
+  for (int e = pptr[k] + threadIdx.x; e < pptr[k + 1]; e += blockDim.x) {
+    const int code = pent[e], r = code >> 1, sd = code & 1;
+    const double xv = xr[r];
+#pragma unroll
+    for (int a = 0; a < NM; ++a) acc[a] += gc[((long long)r * 2 + sd) * NM + a] * xv;
+  }
+  block_sum_multi<256>(acc, NM, sh);
+  if (threadIdx.x == 0 && pptr[k + 1] > pptr[k])
+    for (int a = 0; a < NM; ++a) g[k * NM + a] += acc[a];
+}
+
+afi_status nested_gcoef(afi_ctx *c) {
+  if (!c->n_nest) return AFI_OK;
+  launch(k_nest_gcoef, (unsigned)((c->n_nest + 127) / 128), 128, 0, 0, (const DevPatch *)c->patches,
+         (const double *)c->ctrl, (const int *)c->nest_ptr, (const double *)c->nest_w,
+         (const int4 *)c->nest_eki, (int)c->n_nest, c->dim, c->nm, c->nest_gc);
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
+}
+
+static void nest_B(afi_ctx *c, const double *x, double *yr, double alpha, int acc, cudaStream_t s) {
+  launch(k_nest_B, (unsigned)((c->n_nest + 255) / 256), 256, 0, s, (const int *)c->nest_ptr,
+         (const int *)c->nest_ent, (const double *)c->nest_w, c->n_nest, x, yr, alpha, acc,
+         (const double *)c->gate);
+}
+
+static void nest_Bt(afi_ctx *c, const double *xr, double *y, double alpha, int acc, cudaStream_t s) {
+  launch(k_nest_Bt, (unsigned)((c->n_nd + 255) / 256), 256, 0, s, (const int *)c->nd_dof,
+         (const int *)c->nd_ptr, (const int *)c->nd_ent, (const double *)c->nd_w, c->n_nd, xr, y,
+         alpha, acc, (const double *)c->gate);
+}
+
+static void nest_blockinv(afi_ctx *c, const double *xr, double *yr, cudaStream_t s) {
+  launch(k_nest_blockinv, (unsigned)c->n_nblk, 256, 0, s, (const int *)c->nblk_ptr,
+         (const long long *)c->nblk_off, (const double *)c->nest_binv, xr, yr, (const double *)c->gate);
+}
+
 // dense y = M g (M: n x n), one warp per row.
 __global__ void k_dense_mv(const double *M, const double *g, double *y, int n, const double *gate) {
   if (gate && *gate == 0.0) return;   // inactive MINRES iteration
@@ -400,15 +538,15 @@ __global__ void k_rigid_tables(const DevPatch *P, const double *ctrl, const int2
 }
 
 afi_status rigid_tables(afi_ctx *c) {
-  if (c->n_c == 0) return AFI_OK;
-  AFI_TRY(dalloc(c, (void **)&c->row_cp, (size_t)c->n_c * sizeof(int2)));
-  AFI_TRY(dalloc(c, (void **)&c->row_cv, (size_t)c->n_c * sizeof(double4_32a)));
+  if (c->n_c0 == 0) return AFI_OK;
+  AFI_TRY(dalloc(c, (void **)&c->row_cp, (size_t)c->n_c0 * sizeof(int2)));
+  AFI_TRY(dalloc(c, (void **)&c->row_cv, (size_t)c->n_c0 * sizeof(double4_32a)));
   int ne = 0;
   AFI_CUDA(cudaMemcpy(&ne, c->prow_ptr + c->npatch, sizeof(int), cudaMemcpyDeviceToHost));
   AFI_TRY(dalloc(c, (void **)&c->prow_coef, (size_t)std::max(ne, 1) * sizeof(double2)));
-  const long nt = std::max((long)ne, c->n_c);
+  const long nt = std::max((long)ne, c->n_c0);
   launch(k_rigid_tables, (unsigned)((nt + 255) / 256), 256, 0, 0, (const DevPatch *)c->patches,
-         (const double *)c->ctrl, (const int2 *)c->row_copy, (const int2 *)c->row_patch, c->n_c,
+         (const double *)c->ctrl, (const int2 *)c->row_copy, (const int2 *)c->row_patch, c->n_c0,
          c->row_cp, c->row_cv, (const int *)c->prow_ptr, c->prow_ent, c->prow_coef, c->npatch, c->dim);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
@@ -423,6 +561,14 @@ afi_status op_Gt_rows(afi_ctx *c, const double *x, double *g, cudaStream_t s) {
   else
     launch(k_Gt_part<3>, gr, 256, 0, s, (const int *)c->prow_ptr, (const int2 *)c->prow_ent,
            (const double2 *)c->prow_coef, x, c->part, cnt, g, (const double *)c->gate);
+  if (c->n_nest) {   // the nested rows' share, added after the node rows' sums
+    if (c->nm == 6)
+      launch(k_nest_Gt<6>, c->npatch, 256, 0, s, (const int *)c->pn_ptr, (const int *)c->pn_ent,
+             (const double *)c->nest_gc, x + c->n_c0, g, (const double *)c->gate);
+    else
+      launch(k_nest_Gt<3>, c->npatch, 256, 0, s, (const int *)c->pn_ptr, (const int *)c->pn_ent,
+             (const double *)c->nest_gc, x + c->n_c0, g, (const double *)c->gate);
+  }
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -464,9 +610,14 @@ afi_status op_Pchi(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
 }
 
 static afi_status G_apply(afi_ctx *c, const double *y, double *out, const double *src, cudaStream_t s) {
-  launch(k_G, (unsigned)((c->n_c + 255) / 256), 256, 0, s, (const int2 *)c->row_cp,
-         (const double4_32a *)c->row_cv, c->n_c, y, out, c->dim, c->nm, src ? 1 : 0, src,
-         (const double *)c->gate);
+  if (c->n_c0)
+    launch(k_G, (unsigned)((c->n_c0 + 255) / 256), 256, 0, s, (const int2 *)c->row_cp,
+           (const double4_32a *)c->row_cv, c->n_c0, y, out, c->dim, c->nm, src ? 1 : 0, src,
+           (const double *)c->gate);
+  if (c->n_nest)
+    launch(k_nest_G, (unsigned)((c->n_nest + 255) / 256), 256, 0, s, (const int2 *)c->nest_gk,
+           (const double *)c->nest_gc, c->n_nest, c->nm, y, out + c->n_c0,
+           src ? src + c->n_c0 : (const double *)nullptr, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }
@@ -541,10 +692,19 @@ afi_status op_PS(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
   if (c->n_shell)
     launch(k_Bt_inv, (unsigned)((c->n_shell + 255) / 256), 256, 0, s, (const int *)c->shell_dof,
            (const int *)c->bt_ptr, (const int *)c->bt_ent, (const int2 *)c->row_grp, c->n_shell, x, t1, (const double *)c->gate);
+  if (c->n_nest) {   // nested rows: their block inverse, then B^T onto their dofs
+    nest_blockinv(c, x + c->n_c0, c->nest_tmp, s);
+    nest_Bt(c, c->nest_tmp, t1, 1.0, 0, s);
+  }
   if (c->exact) AFI_TRY(exact_schur(c, t1, t2, s));
   else AFI_TRY(schur_run(c, t1, t2, s));
-  launch(k_B_inv, (unsigned)((c->n_c + 255) / 256), 256, 0, s, (const int2 *)c->row_copy,
-         (const int2 *)c->row_grp, c->n_c, (const double *)t2, y, (const double *)c->gate);
+  if (c->n_c0)
+    launch(k_B_inv, (unsigned)((c->n_c0 + 255) / 256), 256, 0, s, (const int2 *)c->row_copy,
+           (const int2 *)c->row_grp, c->n_c0, (const double *)t2, y, (const double *)c->gate);
+  if (c->n_nest) {
+    nest_B(c, t2, c->nest_tmp, 1.0, 0, s);
+    nest_blockinv(c, c->nest_tmp, y + c->n_c0, s);
+  }
   AFI_LAUNCH_CHECK();
   return AFI_OK;
 }

@@ -1,8 +1,9 @@
 // Context setup: problem validation, univariate tables, patch descriptors,
 // geometry and stiffness assembly, interface connectivity, the constraint
 // matrix B (Section 4, non-redundant rows: one row per copy on the Dirichlet
-// boundary, star rows u_{c1} - u_{cj} elsewhere), rigid modes, R^T R and
-// G^T G with their inverses.  Integer bookkeeping (which copies form a
+// boundary, star rows u_{c1} - u_{cj} elsewhere, then the rows of nested
+// non-conforming faces, nested.cu), rigid modes, R^T R and G^T G with their
+// inverses.  Integer bookkeeping (which copies form a
 // geometric node, the row lists) is done on the host; all floating-point
 // work runs in kernels.
 #include "common.cuh"
@@ -376,6 +377,11 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     if (!(scale > 0.0)) scale = 1.0;
   }
   const double quant = 1e-10 * scale;
+  // nested non-conforming faces: their points off the Dirichlet boundary are
+  // glued by the nested rows (nested.cu), not by coordinates
+  std::vector<NestedFace> nfaces;
+  std::set<std::pair<int, int>> apart;
+  AFI_TRY(nested_detect(c, prob, quant, nfaces, apart));
   struct Item { std::array<long long, 3> key; int k, i; };
   std::vector<Item> items;
   for (int k = 0; k < NP; ++k) {
@@ -387,6 +393,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
           if (D == 3) sh = sh || i3 == 0 || i3 == P.n[2] - 1;
           if (!sh) continue;
           int i = idx3(i1, i2, i3, P.n);
+          if (!apart.empty() && apart.count({k, i})) continue;
           Item it;
           it.key = {0, 0, 0};
           for (int d = 0; d < D; ++d)
@@ -445,6 +452,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
       }
     }
   c->n_c = (long)rc.size();
+  c->n_c0 = c->n_c;
   // B^T CSR over shell dofs, per-patch row lists, pair lists for G^T G
   std::map<int, std::vector<int>> by_dof;
   std::vector<std::vector<int4>> plist(NP);
@@ -486,6 +494,9 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
   AFI_TRY(upload(c, &c->prow_ptr, pptr));
   AFI_TRY(upload(c, &c->prow_ent, pent));
   AFI_TRY(rigid_tables(c));
+  // rows of the nested faces after the node rows, and their G coefficients
+  AFI_TRY(nested_build(c, prob, nfaces));
+  AFI_TRY(nested_gcoef(c));
 
   // ---- G^T G (diagonal blocks from the per-patch lists, off-diagonal from
   //      the patch pairs) and its inverse; R^T R per patch and its inverse
@@ -521,6 +532,7 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     if (npair > 0)
       launch(k_rr_blocks, npair, 256, 0, 0, c->patches, c->ctrl, dptr + ndiag, dkk + ndiag, dent, c->GtG, c->ng, nm, D, 1);
     AFI_LAUNCH_CHECK();
+    AFI_TRY(nested_gtg(c));
     // R^T R per patch
     AFI_TRY(dalloc(c, (void **)&c->RtR_inv, (size_t)NP * nm * nm * sizeof(double)));
     launch(k_RtR, NP, 256, 0, 0, c->patches, c->ctrl, c->RtR_inv, D, nm);
@@ -600,7 +612,12 @@ void free_context(afi_ctx *c) {
                   c->tcsplit[1][1].d_line, c->prow_coef, c->row_cp, c->row_cv, c->ps_buf,
                   c->ps_rint, c->ps_vint, c->xsplit, c->stencil2, c->ex_Kinv, c->ex_AIIinv,
                   c->ex_koff, c->ex_aoff, c->geo_dA, c->geo_dS, c->geo_tmp, c->mws, c->mst,
-                  c->xsplit_multi};
+                  c->xsplit_multi, c->nest_ptr, c->nest_ent, c->nest_w, c->nest_eki, c->nd_dof,
+                  c->nd_ptr, c->nd_ent, c->nd_w, c->nblk_ptr, c->nblk_off, c->nest_binv, c->nest_gk,
+                  c->nest_gc, c->pn_ptr, c->pn_ent, c->nest_tmp, c->tcsplit[0][0].d_pbounds,
+                  c->tcsplit[0][0].d_lbounds, c->tcsplit[0][1].d_pbounds, c->tcsplit[0][1].d_lbounds,
+                  c->tcsplit[1][0].d_pbounds, c->tcsplit[1][0].d_lbounds, c->tcsplit[1][1].d_pbounds,
+                  c->tcsplit[1][1].d_lbounds};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);
