@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256, 3) k_fd_plane(const DevPatch *P, const Ta
         issue_product<FMT>(tmem, A, bm + (m ? slot1 : 0) * bsz, ntile, Kp, Np,
                            (uint32_t)(ntile * 128 + 1) * 16u);
         commit(&mbar);
-        if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
+        if (!wait_phase_backoff(&mbar, (uint32_t)m)) failed = 1;
         asm volatile("tcgen05.fence::before_thread_sync;");
       }
       __syncthreads();
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(256, 3) k_fd_line(const DevPatch *P, const Tab
       if (tid == 0 && !failed) {
         issue_product<FMT>(tmem, A, bm + m * bsz, 1, Kp, Np, (uint32_t)lbo * (uint32_t)sizeof(T));
         commit(&mbar);
-        if (!wait_phase(&mbar, (uint32_t)m)) failed = 1;
+        if (!wait_phase_backoff(&mbar, (uint32_t)m)) failed = 1;
         asm volatile("tcgen05.fence::before_thread_sync;");
       }
       __syncthreads();

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
           mma<FMT>(tmem + (uint32_t)(t * Np), sdesc(a0 + t * 2048u + ks * 2u * lboA, lboA, 128u),
                    sdesc(b0 + ks * 256, 128, sboB), id, ks > 0 ? 1u : 0u);
       commit(&mbar);
-      if (!wait_phase(&mbar, (uint32_t)(m & 1))) failed = 1;
+      if (!wait_phase_backoff(&mbar, (uint32_t)(m & 1))) failed = 1;
       asm volatile("tcgen05.fence::before_thread_sync;");
     }
     __syncthreads();

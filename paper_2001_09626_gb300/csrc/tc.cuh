@@ -66,6 +66,21 @@ __device__ __forceinline__ bool wait_phase(uint64_t *mbar, uint32_t phase) {
   return wait_phase_n(mbar, phase, 1LL << 22, &used);
 }
 
+// The same with a 64 ns sleep between polls, for a single thread waiting on
+// MMAs while the rest of its CTA waits at a barrier: the polls then take
+// fewer issue slots from the other CTAs on the SM (at most 2^22 polls).
+__device__ __forceinline__ bool wait_phase_backoff(uint64_t *mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long long it = 0; it < (1LL << 22) && !done; ++it) {
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(smem_u32(mbar)), "r"(phase));
+    if (!done) __nanosleep(64);
+  }
+  return done != 0;
+}
+
 // 32 lanes x 8 columns of 32 bits from tensor memory; completes at ld_wait()
 __device__ __forceinline__ void ld8(uint32_t taddr, uint32_t *r) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
