@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256, 3) k_fd_plane(const DevPatch *P, const Ta
       }
     }
     if (reload) {   // the B operands have landed
-      if (tid == 0 && !wait_phase(&tma_bar, tma_phase)) failed = 1;
+      if (tid == 0 && !wait_phase_backoff(&tma_bar, tma_phase)) failed = 1;
       tma_phase ^= 1u;
       key = nkey;
     }
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(256, 3) k_fd_line(const DevPatch *P, const Tab
       }
     }
     if (reload) {   // the B operands have landed
-      if (tid == 0 && !wait_phase(&tma_bar, tma_phase)) failed = 1;
+      if (tid == 0 && !wait_phase_backoff(&tma_bar, tma_phase)) failed = 1;
       tma_phase ^= 1u;
       key = t2;
     }

@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_fd_tc(const DevPatch *P, cons
       }
     }
   }
-  if (tid == 0 && !wait_phase(&tma_bar, 0)) failed = 1;   // B operands have landed
+  if (tid == 0 && !wait_phase_backoff(&tma_bar, 0)) failed = 1;   // B operands have landed
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
                  "r"(tcols));

@@ -196,8 +196,9 @@ __device__ __forceinline__ RigidNZ rigid_nz(int comp, const double *X, int dim) 
 
 constexpr int kCounters = 3072;  // block tickets of the last-block reductions, in c->small
 constexpr int kGtBlocks = 4;    // blocks per patch for the row-list reduction
-constexpr int kRtChunks = 16;   // blocks per (patch, component) for R^T v (partials:
-                                 // dim * 16 * 3 <= the 320 per patch of the P_u slice)
+constexpr int kRtChunksMax = 16;   // blocks per (patch, component) for R^T v, at most
+                                   // (partials: dim * 16 * 3 <= the 320 per patch of
+                                   // the P_u slice); about one per 8192 nodes, at least 4
 
 // After each block has written its partials: true (in every thread) in the
 // block that finishes last, which then combines all partials; it resets the
@@ -580,7 +581,8 @@ static double *pu_part(afi_ctx *c) { return c->part + 64LL * c->npatch; }
 
 static afi_status Rt_apply(afi_ctx *c, const double *x, double *g, const double *Minv, cudaStream_t s) {
   unsigned *cnt = reinterpret_cast<unsigned *>(c->small + kCounters) + 3;
-  launch(k_Rt_part, dim3(kRtChunks, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x, pu_part(c),
+  const int chunks = std::min(kRtChunksMax, std::max(4, (int)((c->max_N + 8191) / 8192)));
+  launch(k_Rt_part, dim3(chunks, c->dim, c->npatch), 256, 0, s, c->patches, c->ctrl, x, pu_part(c),
          c->dim, cnt, c->nm, g, Minv, (const double *)c->gate);
   AFI_LAUNCH_CHECK();
   return AFI_OK;

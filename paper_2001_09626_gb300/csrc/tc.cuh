@@ -67,8 +67,9 @@ __device__ __forceinline__ bool wait_phase(uint64_t *mbar, uint32_t phase) {
 }
 
 // The same with a 64 ns sleep between polls, for a single thread waiting on
-// MMAs while the rest of its CTA waits at a barrier: the polls then take
-// fewer issue slots from the other CTAs on the SM (at most 2^22 polls).
+// MMAs or bulk copies while the rest of its CTA waits at a barrier: the polls
+// then take fewer issue slots from the other CTAs on the SM (at most 2^22
+// polls).
 __device__ __forceinline__ bool wait_phase_backoff(uint64_t *mbar, uint32_t phase) {
   uint32_t done = 0;
   for (long long it = 0; it < (1LL << 22) && !done; ++it) {
