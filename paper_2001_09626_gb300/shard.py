@@ -20,7 +20,11 @@ a rank's own patches; on GPUs they are the library's kernels on a context
 that holds those patches.  Exchanges use torch.distributed (NCCL across GPUs,
 gloo on CPU).  The constraint rows are the library's (dof A, dof B or -1),
 one star row u_A - u_B per additional copy of a node, or e_A for a copy on
-the Dirichlet boundary (reading 1 of the design notes)."""
+the Dirichlet boundary (reading 1 of the design notes).  The rows of nested
+non-conforming faces (a fine copy tied to several coarse ones with
+knot-insertion weights) are not covered: a sharded form would give each
+nested face's rows to the fine patch's owner and bring the coarse face's
+values in by the same kind of halo."""
 from __future__ import annotations
 
 import math
