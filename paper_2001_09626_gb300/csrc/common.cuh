@@ -155,6 +155,7 @@ struct TcSplit {
   int nplane = 0, nline = 0;
   int *d_pbounds = nullptr, *d_lbounds = nullptr;   // persistent CTAs' ranges of the lists
   int pgrid = 0, lgrid = 0;                         // persistent CTAs per (component, rhs)
+  int per = 2;                                      // three-pass work items per CTA (tuned)
   int cap_p = 0, bsz_p = 0, tcols_p = 32, cap_l = 0, bsz_l = 0, tcols_l = 32;
   size_t smem_p = 0, smem_l = 0;
 };
@@ -365,7 +366,7 @@ afi_status geo_scale(afi_ctx *c, const double *x, const double *d, double *y, lo
 // fd_slab.cu (three-pass tensor-core FD for tensors larger than one CTA)
 afi_status slab_prepare(afi_ctx *c, int *dyn_max);
 afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> &cand,
-                      std::vector<int> &rest, TcSplit &sp, int dyn_max);
+                      std::vector<int> &rest, TcSplit &sp, int dyn_max, int per);
 afi_status slab_run(afi_ctx *c, int interior, int fmt, const TcSplit &sp, const double *r,
                     double *s, cudaStream_t st, int nrhs);
 

@@ -610,16 +610,19 @@ std::vector<int> balanced_ranges(const std::vector<long long> &cost, int nb) {
 }
 
 // CTAs per (component, right-hand side): at least the resident CTAs of the
-// whole GPU shared over the components, and about two items per CTA, so that
-// a CTA's setup (tensor memory, barriers, B operands) is shared by a few
+// whole GPU shared over the components, and about `per` items per CTA, so
+// that a CTA's setup (tensor memory, barriers, B operands) is shared by a few
 // items while CTAs that finish early are replaced by waiting ones (a single
-// wave of long ranges measured 35% slower with one right-hand side).
+// wave of long ranges measured 35% slower with one right-hand side; 2 to 4
+// items did best, which of them depends on the shapes: the FD split tuner
+// times both).
 template <typename K>
-afi_status persistent_grid(afi_ctx *c, K kern, size_t smem, int nitems, int *grid) {
+afi_status persistent_grid(afi_ctx *c, K kern, size_t smem, int nitems, int per, int *grid) {
   int occ = 0;
   AFI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem));
   const int wave = c->nsm * std::max(occ, 1) / std::max(c->dim, 1);
-  *grid = std::max(1, std::min(nitems, std::max(wave, (nitems + 1) / 2)));
+  per = std::max(1, per);
+  *grid = std::max(1, std::min(nitems, std::max(wave, (nitems + per - 1) / per)));
   return AFI_OK;
 }
 
@@ -629,7 +632,7 @@ afi_status persistent_grid(afi_ctx *c, K kern, size_t smem, int nitems, int *gri
 // the SIMT kernel) and build the pass work lists and the persistent CTAs'
 // ranges of them.
 afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> &cand,
-                      std::vector<int> &rest, TcSplit &sp, int dyn_max) {
+                      std::vector<int> &rest, TcSplit &sp, int dyn_max, int per) {
   std::vector<int4> pw;
   std::vector<int2> lw;
   std::vector<long long> pcost, lcost;
@@ -677,11 +680,11 @@ afi_status slab_build(afi_ctx *c, int interior, int fmt, const std::vector<int> 
     AFI_TRY(dalloc(c, (void **)&sp.d_line, lw.size() * sizeof(int2)));
     AFI_CUDA(cudaMemcpy(sp.d_line, lw.data(), lw.size() * sizeof(int2), cudaMemcpyHostToDevice));
     if (fmt == 2) {
-      AFI_TRY(persistent_grid(c, k_fd_plane<2, 0>, sp.smem_p, sp.nplane, &sp.pgrid));
-      AFI_TRY(persistent_grid(c, k_fd_line<2>, sp.smem_l, sp.nline, &sp.lgrid));
+      AFI_TRY(persistent_grid(c, k_fd_plane<2, 0>, sp.smem_p, sp.nplane, per, &sp.pgrid));
+      AFI_TRY(persistent_grid(c, k_fd_line<2>, sp.smem_l, sp.nline, per, &sp.lgrid));
     } else {
-      AFI_TRY(persistent_grid(c, k_fd_plane<1, 0>, sp.smem_p, sp.nplane, &sp.pgrid));
-      AFI_TRY(persistent_grid(c, k_fd_line<1>, sp.smem_l, sp.nline, &sp.lgrid));
+      AFI_TRY(persistent_grid(c, k_fd_plane<1, 0>, sp.smem_p, sp.nplane, per, &sp.pgrid));
+      AFI_TRY(persistent_grid(c, k_fd_line<1>, sp.smem_l, sp.nline, per, &sp.lgrid));
     }
     const std::vector<int> pb = balanced_ranges(pcost, sp.pgrid), lb = balanced_ranges(lcost, sp.lgrid);
     AFI_TRY(dalloc(c, (void **)&sp.d_pbounds, pb.size() * sizeof(int)));

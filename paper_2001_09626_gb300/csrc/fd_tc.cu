@@ -349,7 +349,8 @@ static size_t tc_smem(int cap, int bsz, int tcols, int nslot, int fmt) {
 // the rest go to the three-pass kernels, else to the SIMT kernel.  One launch
 // gives every CTA the shared memory of the largest tensor in the list, so a
 // low thr keeps the small tensors' residency high.
-static afi_status build_split_thr(afi_ctx *c, int interior, int fmt, size_t thr, TcSplit &sp) {
+static afi_status build_split_thr(afi_ctx *c, int interior, int fmt, size_t thr, TcSplit &sp,
+                                  int per) {
   std::vector<std::pair<size_t, int>> order;
   const bool force_slab = (c->opt.variant & AFI_VARIANT_FD_SLAB) != 0;
   for (int k = 0; k < c->npatch; ++k) {
@@ -375,7 +376,8 @@ static afi_status build_split_thr(afi_ctx *c, int interior, int fmt, size_t thr,
     else big.push_back(k);
   }
   // tensors too large for one CTA: three-pass slab kernels, else SIMT
-  AFI_TRY(slab_build(c, interior, fmt, big, simt, sp, g_slab_dyn_max));
+  AFI_TRY(slab_build(c, interior, fmt, big, simt, sp, g_slab_dyn_max, per));
+  sp.per = per;
   int maxN = 1;
   for (int k : simt) maxN = std::max(maxN, interior ? c->hp[k].Ni : c->hp[k].N);
   sp.ntc = (int)tc.size();
@@ -409,11 +411,13 @@ static afi_status run_split(afi_ctx *c, int interior, int fmt, const TcSplit &sp
 
 // Project-written autotuner of the FD work split, per (interior, operand
 // format): every distinct shared-memory need of the tensors that fit one CTA
-// is a candidate threshold (tensors above it take the three-pass kernels);
-// each candidate's split is timed on one application (best of three after
-// a warm-up) and the fastest kept.  A single candidate (tensors of one
-// shape) needs no timing.  AFI_VARIANT_FD_FIXED keeps every tensor that fits
-// one CTA in the single-CTA kernel instead.
+// is a candidate threshold (tensors above it take the three-pass kernels),
+// and the three-pass kernels take 2 or 4 work items per CTA; each
+// combination with work for the three-pass kernels (or the single-CTA split
+// alone) is timed on one application (best of three after a warm-up) and
+// the fastest kept.  A batch with one combination needs no timing.
+// AFI_VARIANT_FD_FIXED keeps every tensor that fits one CTA in the
+// single-CTA kernel and two items per three-pass CTA instead.
 static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
   const size_t all = (size_t)-1;
   std::vector<size_t> cand;
@@ -426,8 +430,19 @@ static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
   cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
   const bool fixed = (c->opt.variant & (AFI_VARIANT_FD_FIXED | AFI_VARIANT_FD_SLAB)) != 0 ||
                      c->dim != 3;
-  if (fixed || cand.size() <= 1) return build_split_thr(c, interior, fmt, all, sp);
-  cand.insert(cand.begin(), 0);   // every 3D tensor through the three-pass kernels
+  if (fixed) return build_split_thr(c, interior, fmt, all, sp, 2);
+  std::vector<size_t> thrs;
+  if (cand.size() > 1) {
+    thrs.push_back(0);   // every 3D tensor through the three-pass kernels
+    thrs.insert(thrs.end(), cand.begin(), cand.end());
+  } else {
+    thrs.push_back(all);
+  }
+  if (thrs.size() == 1) {   // one split: time the items per CTA only if it has three-pass work
+    AFI_TRY(build_split_thr(c, interior, fmt, all, sp, 2));
+    if (sp.nplane == 0) return AFI_OK;
+    free_split(sp);
+  }
   const long long n = interior ? c->n_int : c->n_dof;
   double *buf = nullptr;
   AFI_CUDA(cudaMalloc(&buf, (size_t)2 * n * sizeof(double)));
@@ -440,29 +455,35 @@ static afi_status build_split(afi_ctx *c, int interior, int fmt, TcSplit &sp) {
   afi_status st = AFI_OK;
   float best = 1e30f;
   size_t bthr = all;
-  for (size_t thr : cand) {
-    TcSplit tmp;
-    st = build_split_thr(c, interior, fmt, thr, tmp);
-    float tmin = 1e30f;
-    for (int rep = 0; rep < 4 && st == AFI_OK; ++rep) {
-      cudaEventRecord(e0, 0);
-      st = run_split(c, interior, fmt, tmp, buf, buf + n, 0, 1);
-      cudaEventRecord(e1, 0);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) tmin = std::min(tmin, ms);
+  int bper = 2;
+  for (size_t thr : thrs)
+    for (int per : {2, 4}) {
+      TcSplit tmp;
+      st = build_split_thr(c, interior, fmt, thr, tmp, per);
+      if (st == AFI_OK && per != 2 && tmp.nplane == 0) {   // no three-pass work: same split as per 2
+        free_split(tmp);
+        continue;
+      }
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 4 && st == AFI_OK; ++rep) {
+        cudaEventRecord(e0, 0);
+        st = run_split(c, interior, fmt, tmp, buf, buf + n, 0, 1);
+        cudaEventRecord(e1, 0);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tmin = std::min(tmin, ms);
+      }
+      free_split(tmp);
+      if (st != AFI_OK) break;
+      if (tmin < best) { best = tmin; bthr = thr; bper = per; }
     }
-    free_split(tmp);
-    if (st != AFI_OK) break;
-    if (tmin < best) { best = tmin; bthr = thr; }
-  }
   c->gate = gate;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(buf);
   AFI_TRY(st);
-  return build_split_thr(c, interior, fmt, bthr, sp);
+  return build_split_thr(c, interior, fmt, bthr, sp, bper);
 }
 
 afi_status fd_tc_prepare(afi_ctx *c) {
