@@ -71,14 +71,17 @@ __device__ __forceinline__ float f64_to_f32(double x) {
 }
 
 // f32 -> f64: exact for normal numbers, zero and infinities; FP32
-// subnormals flush to signed zero, NaN stays NaN.
+// subnormals flush to signed zero, NaN becomes the quiet NaN.  Written
+// without branches: the magnitude's bits shifted into place and the
+// exponent rebiased by 1023 - 127 in one add, then selects for the ends.
 __device__ __forceinline__ double f32_to_f64(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-  unsigned hi = sign | ((e + 896u) << 20) | (m >> 3), lo = m << 29;
-  if (e == 0u) { hi = sign; lo = 0u; }
-  if (e == 0xFFu) hi = sign | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
-  return __hiloint2double((int)hi, (int)lo);
+  const unsigned u = __float_as_uint(f), mag = u & 0x7FFFFFFFu;
+  unsigned hi = (mag >> 3) + (896u << 20), lo = u << 29;
+  const bool tiny = mag < 0x00800000u, special = mag >= 0x7F800000u;
+  hi = tiny ? 0u : hi;
+  lo = (tiny || special) ? 0u : lo;
+  hi = special ? (mag > 0x7F800000u ? 0x7FF80000u : 0x7FF00000u) : hi;
+  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
 }
 
 // ------------------------------------------------------- 1D spline tables

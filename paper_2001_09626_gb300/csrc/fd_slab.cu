@@ -281,16 +281,29 @@ __global__ void __launch_bounds__(256, 3) k_fd_plane(const DevPatch *P, const Ta
           const int jn = min(8, na - j0);
           if (m == 0) {
             T *dst = A + kslab<FMT>(j0 + n1 * zl, b, lbo1);
+            if (jn == 8) {   // a full chunk: no per-column predicate
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj)
-              if (jj < jn) dst[jj * T16] = Op<FMT>::cvt(__uint_as_float(raw[jj]));
+              for (int jj = 0; jj < 8; ++jj) dst[jj * T16] = Op<FMT>::cvt(__uint_as_float(raw[jj]));
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj)
+                if (jj < jn) dst[jj * T16] = Op<FMT>::cvt(__uint_as_float(raw[jj]));
+            }
           } else {
             const long long ob = base + (long long)zl * plane + b + (long long)j0 * n1;
+            if (jn == 8) {
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              if (jj < jn) {
+              for (int jj = 0; jj < 8; ++jj) {
                 if (BACK) st_out(s + ob + (long long)jj * n1, __uint_as_float(raw[jj]));
                 else st_out(scr + ob + (long long)jj * n1, __uint_as_float(raw[jj]));
+              }
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {
+                if (jj < jn) {
+                  if (BACK) st_out(s + ob + (long long)jj * n1, __uint_as_float(raw[jj]));
+                  else st_out(scr + ob + (long long)jj * n1, __uint_as_float(raw[jj]));
+                }
               }
             }
           }

@@ -92,20 +92,34 @@ __device__ __forceinline__ void fd_epilogue(uint32_t tmem, typename tc::Op<FMT>:
       const int jn = min(8, na - j0);
       if (KIND == 2) {
         double *o = so + line + jstride * j0;
+        if (jn == 8) {   // a full chunk: no per-column predicate
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj)
-          if (jj < jn) o[jstride * jj] = f32_to_f64(__uint_as_float(raw[jj]));
+          for (int jj = 0; jj < 8; ++jj) o[jstride * jj] = f32_to_f64(__uint_as_float(raw[jj]));
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj)
+            if (jj < jn) o[jstride * jj] = f32_to_f64(__uint_as_float(raw[jj]));
+        }
       } else {
         // element (row = c + nc j, k = b) of the next operand
         typename Op<FMT>::T *dst = A + kslab<FMT>(c + nc * j0, b, lbo);
         float lb = 0.f;
         if (KIND == 1) lb = sc.s0 + sc.sb * sc.D0[b] + sc.sc * sc.D1[c];
+        if (jn == 8) {   // a full chunk: no per-column predicate
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          if (jj < jn) {
+          for (int jj = 0; jj < 8; ++jj) {
             float x = __uint_as_float(raw[jj]);
             if (KIND == 1) x = __fdividef(x, lb + sc.sj * sc.D2[j0 + jj]);
             dst[jj * jstep] = Op<FMT>::cvt(x);
+          }
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            if (jj < jn) {
+              float x = __uint_as_float(raw[jj]);
+              if (KIND == 1) x = __fdividef(x, lb + sc.sj * sc.D2[j0 + jj]);
+              dst[jj * jstep] = Op<FMT>::cvt(x);
+            }
           }
         }
       }
