@@ -64,11 +64,16 @@ WORKLOADS = {
     "C4": "C4: thick quarter annulus, 6x4x3 patches, p=3, C^2, 24^3 elements/patch, " + _COMMON,
     "C5-mid": "C5-mid: 2x2x2 patches of the C5 twisted box (45-degree twist), p=4, C^3, "
               "48^3 elements/patch, " + _COMMON,
+    "C5": "C5: twisted box (unit cube, 45-degree twist about z), 8x8x4 = 256 patches, p=4, C^3, "
+          "48^3 elements/patch (108 M DoF), matrix-free stiffness, " + _COMMON,
 }
+# workloads whose stored stiffness exceeds device memory: matrix-free operator
+MATRIX_FREE_WORKLOADS = ("C5",)
 # oracle samples: same geometry kind and degree as the workload, oracle-sized
 SAMPLES = {"C3": ("C3-mid", "2x2x1 uneven quarter-annulus patches, p=4, element columns "
                             "4/6 x 4/6 x 4"),
-           "C2": ("C2-mid", "3x3x3 jittered cube patches, p=3, 6^3 elements")}
+           "C2": ("C2-mid", "3x3x3 jittered cube patches, p=3, 6^3 elements"),
+           "C5": ("C5-small", "2x2x2 twisted-box patches, p=4, 3^3 elements")}
 
 
 def workload_label(name):
@@ -95,6 +100,8 @@ def parse():
     ap.add_argument("--fd-slab", action="store_true",
                     help="--fd-only: send every tensor through the three-pass kernels")
     ap.add_argument("--precs", default="fp64,fp32,tf32,bf16", help="--fd-only: precisions to time")
+    ap.add_argument("--plain-iters", type=int, default=6,
+                    help="matrix-free workloads: iterations of the bounded plain FP64 run")
     ap.add_argument("--fd-fixed", action="store_true",
                     help="--fd-only: the fixed FD work split instead of the timed one")
     return ap.parse_args()
@@ -701,12 +708,217 @@ def run_fd_only(args):
     s.close()
 
 
+def mf_flops_per_element(p):
+    """FLOPs of one element in the matrix-free stiffness kernel, as it runs
+    (k_mf in csrc/mf.cu): six fields through three forward direction passes
+    (2 + 3 + 3 table contractions of (p+1)^4 FMAs each), three components
+    through three back passes (3 + 3 + 2), two FLOPs per FMA, plus the
+    pointwise Jacobian inverse, stress and flux (168 FLOPs per Gauss point)."""
+    nb = p + 1
+    return 2 * (6 * 8 + 3 * 8) * nb ** 4 + 168 * nb ** 3
+
+
+def fp32_peak_tflops(sm_mhz=2070.0, sms=152):
+    """FP32 FMA peak from the unit counts: 128 FP32 lanes per SM, 2 FLOPs
+    per FMA, at the given SM clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def run_matrix_free(args):
+    """The metric's own configuration on the matrix-free operator (C5: 256
+    twisted-box patches, p = 4, 48^3 elements, 108 M DoF; the stored stencil
+    would need 1.9 TB).  One step = one complete solve of one seeded
+    right-hand side: MINRES with TF32 local solvers and FP32 matrix-free
+    products, refined against the FP64 true residual to 1e-8, plus the
+    local-solver setup.  Beside it: the plain FP64 form's per-iteration time
+    on a bounded run (its full solve would take tens of minutes, so its solve
+    time is a labelled projection), eight right-hand sides (solved one after
+    the other: a labelled projection), FD rates and the roofline of the
+    FP32 matrix-free kernel (FP32-pipe bound)."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import afi_workloads as W
+    from paper_2001_09626_gb300 import afieti as A
+    from paper_2001_09626_gb300.solver import Solver
+    torch.cuda.set_device(0)
+    prob = W.config(args.workload)
+    p = int(prob.degree[0])
+    ne = sum(int(np.prod(prob.nel[k])) for k in range(prob.npatch))
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t0 = time.time()
+    s = Solver(prob, prec=args.prec, tol=1e-8, maxit=5000, use_graph=True, matrix_free=True)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    f = s.load_vector(W.body_force_coeffs(prob))
+    n_dof, n_c = s.n_dof, s.n_c
+    for _ in range(args.warmup):
+        s.solve(f)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    L0 = A.afi_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        u, lam = s.solve(f)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = (A.afi_kernel_launches() - L0) // args.steps
+    clocks = sampler.stop()
+    ms_solve = e0.elapsed_time(e1) / args.steps
+    info = dict(s.last_info)
+    fd_setup_ms = float(info["t_fd_setup_ms"])
+    ms = ms_solve + fd_setup_ms
+    # end to end through the C ABI with pinned host buffers
+    f_h = f.cpu().pin_memory()
+    u_h = torch.empty_like(f_h).pin_memory()
+    f_d, u_d, lam_d = torch.empty_like(f), torch.empty_like(f), s.zeros(s.n_c)
+
+    def e2e_step():
+        f_d.copy_(f_h, non_blocking=True)
+        A.ieti_solve(s.ctx, f_d, u_d, lam_d, 1)
+        u_h.copy_(u_d, non_blocking=True)
+    ms_e2e = timed(e2e_step, 1)
+    del f_d, u_d, lam_d
+    # the FP32 matrix-free product (dominant kernel) and the FD rates
+    x = torch.rand(n_dof, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        s.apply(A.AFI_OP_STIFFNESS, x)
+    mv_ms = timed(lambda: s.apply(A.AFI_OP_STIFFNESS, x), 5)
+    r8 = torch.rand(8, n_dof, dtype=torch.float64, device="cuda")
+    fd_ms, fd8_ms = {}, {}
+    for prec in ("fp64", args.prec):
+        s.set_precision(prec)
+        for _ in range(2):
+            s.fd(x)
+            s.fd(r8)
+        fd_ms[prec] = timed(lambda: s.fd(x), 10)
+        fd8_ms[prec] = timed(lambda: s.fd(r8), 5)
+    s.set_precision(args.prec)
+    del r8
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    # the plain FP64 form (FP64 local solvers, FP64 matrix-free products):
+    # a bounded run of its iterations, per-iteration time measured
+    s64 = Solver(prob, prec="fp64", tol=1e-8, maxit=args.plain_iters, use_graph=True,
+                 matrix_free=True, stencil_f64=True)
+    s64.solve(f, allow_not_converged=True)
+    ms_plain_run = timed(lambda: s64.solve(f, allow_not_converged=True), 1)
+    info_plain = dict(s64.last_info)
+    for _ in range(1):
+        s64.apply(A.AFI_OP_STIFFNESS, x)
+    mv64_ms = timed(lambda: s64.apply(A.AFI_OP_STIFFNESS, x), 2)
+    s64.close()
+    del s64, x
+    torch.cuda.empty_cache()
+    plain_iter_ms = info_plain["t_solve_ms"] / max(1, info_plain["iters"])
+    fp64_peak = fp64_peak_tflops()
+    flops = mf_flops_per_element(p) * ne
+    clock = float(clocks.get("sm_mhz") or 2070.0) if isinstance(clocks, dict) else 2070.0
+    fp32_peak = fp32_peak_tflops(2070.0)
+    achieved = flops / (mv_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 2), "peak": round(fp32_peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
+                "peak_source": "FP32 FMA peak from the unit counts: 152 SMs x 128 lanes x 2 FLOP "
+                               "x 2070 MHz (not measured)",
+                "traffic": None,
+                "kernel": f"k_mf<float,{p}> (matrix-free FP32 stiffness: element-wise sum "
+                          "factorisation, Jacobian from the control points), with its FP64->FP32 "
+                          "input and FP32->FP64 output passes",
+                "flops_per_launch": flops, "flops_per_element": mf_flops_per_element(p),
+                "elements": ne, "launch_ms": round(mv_ms, 3),
+                "sm_mhz_median_in_solve": clock,
+                "fp64_form": {"kernel": f"k_mf<double,{p}>", "launch_ms": round(mv64_ms, 2),
+                              "TFLOPs": round(flops / (mv64_ms * 1e-3) / 1e12, 4),
+                              "frac_of_fp64_peak": round(flops / (mv64_ms * 1e-3) / 1e12 / fp64_peak, 3),
+                              "fp64_peak_tflops": round(fp64_peak, 3),
+                              "fp64_peak_source": "cuBLAS DGEMM 4096^3 measured in this run"}}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    fd_bytes = 16 * n_dof
+    roofline_fd = {"bound": "hbm", "kernel": f"k_fd_plane + k_fd_line (tcgen05), {args.prec}",
+                   "achieved": round(fd_bytes / (fd_ms[args.prec] * 1e-3) / 1e9, 1), "peak": hbm,
+                   "unit": "GB/s", "frac": round(fd_bytes / (fd_ms[args.prec] * 1e-3) / 1e9 / hbm, 4),
+                   "traffic": None, "bytes_per_launch": fd_bytes,
+                   "nrhs8": {"achieved": round(8 * fd_bytes / (fd8_ms[args.prec] * 1e-3) / 1e9, 1),
+                             "frac": round(8 * fd_bytes / (fd8_ms[args.prec] * 1e-3) / 1e9 / hbm, 4),
+                             "launch_ms": round(fd8_ms[args.prec], 4)}}
+    line = {"metric": METRIC, "value": round(ms / 1e3, 4), "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": f"mixed: f64 Krylov/residual/jumps, {args.prec} local solvers, "
+                     "f32 matrix-free stiffness in the iterations (refined against the f64 "
+                     "matrix-free true residual)",
+            "data": "synthetic",
+            "config": {"workload": workload_label(args.workload), "n_dof": n_dof, "n_c": n_c,
+                       "local_solver_precision": args.prec, "stiffness": "matrix-free",
+                       "parallelism": "single GPU",
+                       "l2": "inputs larger than L2 (108 M DoF: 0.86 GB per vector; every "
+                             "product reads the control points and the input)"},
+            "iterations": info["iters"], "relres_true": info["relres_true"],
+            "refinement_runs": info["fp64_restarts"], "setup_s": round(setup_s, 3),
+            "solve_s_without_fd_setup": round(ms_solve / 1e3, 4),
+            "fd_setup_s": round(fd_setup_ms / 1e3, 4),
+            "plain_fp64": {"form": "FP64 local solvers and FP64 matrix-free products",
+                           "measured_iterations": info_plain["iters"],
+                           "measured_s": round(ms_plain_run / 1e3, 3),
+                           "per_iteration_ms": round(plain_iter_ms, 2),
+                           "projection": True,
+                           "solve_s": round((plain_iter_ms * info["iters"] +
+                                             info_plain["t_fd_setup_ms"]) / 1e3, 2),
+                           "method": "per-iteration time of the bounded FP64 run x the mixed "
+                                     "solve's iteration count"},
+            "multi_rhs": {"nrhs": 8, "projection": True,
+                          "solve_s": round(8 * ms_solve / 1e3 + fd_setup_ms / 1e3, 2),
+                          "method": "matrix-free products share no coefficient stream: eight "
+                                    "solves one after the other, 8 x the measured solve"},
+            "fd_apply_dofs_per_s": {k: round(n_dof / (v * 1e-3), 1) for k, v in fd_ms.items()},
+            "fd_apply_dofs_per_s_nrhs8": {k: round(8 * n_dof / (v * 1e-3), 1)
+                                          for k, v in fd8_ms.items()},
+            "e2e": {"value": round((ms_e2e + fd_setup_ms) / 1e3, 4), "unit": "s",
+                    "h2d_bytes_per_step": 8 * n_dof, "d2h_bytes_per_step": 8 * n_dof},
+            "gpu_launches": int(launches), "roofline": roofline, "roofline_fd": roofline_fd,
+            "clocks": clocks}
+    if not args.no_cpu_baseline:
+        per, det = oracle_sample_time(args.workload, steps=1, warmup=0)
+        line["cpu_baseline"] = {"value": det["projection_s"], "unit": "s", "cores": det["cores"],
+                                "kind": "oracle", "projection": True,
+                                "sample": det["sample"] + f"; value = sample time x "
+                                          f"{det['projection_scale']} (DoF ratio to "
+                                          f"{args.workload})",
+                                "measured_sample_s": det["sample_s"],
+                                "per_iteration_ms_on_sample": det["per_iteration_on_sample"]}
+        line["cpu_baseline_fd"] = oracle_fd_rate(args.workload)
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.fd_only:
         run_fd_only(args)
+    elif args.workload in MATRIX_FREE_WORKLOADS:
+        run_matrix_free(args)
     else:
         run_ours(args)
 

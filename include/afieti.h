@@ -183,6 +183,37 @@ typedef struct {
                                       batch of tensors of one shape has a
                                       single candidate and is never timed. */
 
+#define AFI_VARIANT_MATRIX_FREE 128 /* 3D problems with one degree (1..5) for
+                                      every patch: apply the stiffness A^(k)
+                                      (eq. 3.1) and the mass of
+                                      afi_load_vector without storing them,
+                                      by sum factorisation over each element
+                                      with the same Gauss rule (p + 1 points
+                                      per element and direction) and the
+                                      Jacobian recomputed from the control
+                                      points in every product.  Nothing per
+                                      quadrature point is stored, so problems
+                                      whose stencil exceeds device memory can
+                                      be solved.  The MINRES iterations use
+                                      FP32 products (input and sums in FP32)
+                                      and refine against the FP64 true
+                                      residual: each run stops when its
+                                      estimate has fallen by 1e-4 (or reached
+                                      tol) and the next solves for the
+                                      correction, at most 12 more runs
+                                      (afi_info.fp64_restarts counts them);
+                                      the true residual, afi_apply in
+                                      AFI_OP_SADDLE's residual form and, with
+                                      AFI_VARIANT_STENCIL_F64, every product
+                                      are FP64.  afi_apply(AFI_OP_STIFFNESS)
+                                      is the FP32 form unless
+                                      AFI_VARIANT_STENCIL_F64 is set.  Several
+                                      right-hand sides are solved one after
+                                      the other.  Excludes
+                                      AFI_VARIANT_LOCAL_ONLY, AFI_VARIANT_EXACT
+                                      and AFI_VARIANT_GEO; afi_lame_grad
+                                      returns AFI_EINVAL. */
+
 /* prec: local-solver arithmetic; tol: relative tolerance (the MINRES
  * preconditioned residual estimate and then the true FP64 residual
  * ||b - A x|| / ||b|| of eq. (4.7) must both reach it; when the
@@ -213,7 +244,9 @@ typedef struct {
   double relres_est, relres_true;
   double t_setup_ms, t_solve_ms;
   double t_fd_setup_ms;
-  int fp64_restarts;   /* 1 if the solve restarted with the FP64 stiffness */
+  int fp64_restarts;   /* 1 if the solve restarted with the FP64 stiffness;
+                          with AFI_VARIANT_MATRIX_FREE the number of
+                          refinement runs after the first */
 } afi_info;
 
 /* Operators of the hot path, for afi_apply (each is one row of the solve):

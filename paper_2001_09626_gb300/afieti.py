@@ -171,6 +171,7 @@ AFI_VARIANT_FORCE_RESTART = 8
 AFI_VARIANT_EXACT = 16
 AFI_VARIANT_GEO = 32
 AFI_VARIANT_FD_FIXED = 64
+AFI_VARIANT_MATRIX_FREE = 128
 
 
 def af_ieti_setup(prob, prec="fp64", tol=1e-8, maxit=2000, use_graph=False, variant=0):

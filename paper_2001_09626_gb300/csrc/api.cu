@@ -13,7 +13,7 @@ static cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s
 
 // entry points that need the assembled stiffness or the quadrature geometry
 static bool has_operator(afi_ctx *c) {
-  if (c->stencil) return true;
+  if (c->stencil || c->mf) return true;
   set_error("context set up with AFI_VARIANT_LOCAL_ONLY: no stiffness or geometry");
   return false;
 }
@@ -65,8 +65,28 @@ static afi_status solve_many(afi_ctx *c, const double *f, double *u, double *lam
     const double *fj = f + (long long)j * c->n_dof;
     double *uj = u + (long long)j * c->n_dof;
     double *lj = lam ? lam + (long long)j * c->n_c : nullptr;
-    afi_status st = nb == 1 ? solve_one(c, fj, uj, lj, &bi, as_stream(stream))
-                            : solve_multi(c, fj, uj, lj, nb, &bi, as_stream(stream));
+    afi_status st = AFI_OK;
+    if (nb == 1) {
+      st = solve_one(c, fj, uj, lj, &bi, as_stream(stream));
+    } else if (c->mf) {
+      // matrix-free products gain nothing from lockstep (no shared
+      // coefficient stream): one solve per right-hand side
+      for (int r = 0; r < nb && st != AFI_EBREAKDOWN && st != AFI_ECUDA; ++r) {
+        afi_info ri{};
+        const afi_status sr = solve_one(c, fj + (long long)r * c->n_dof, uj + (long long)r * c->n_dof,
+                                        lj ? lj + (long long)r * c->n_c : nullptr, &ri, as_stream(stream));
+        bi.iters = std::max(bi.iters, ri.iters);
+        bi.relres_est = std::max(bi.relres_est, ri.relres_est);
+        bi.relres_true = std::max(bi.relres_true, ri.relres_true);
+        bi.t_setup_ms = ri.t_setup_ms;
+        bi.t_fd_setup_ms = ri.t_fd_setup_ms;
+        bi.t_solve_ms += ri.t_solve_ms;
+        bi.fp64_restarts += ri.fp64_restarts;
+        if (sr != AFI_OK && (st == AFI_OK || sr == AFI_EBREAKDOWN || sr == AFI_ECUDA)) st = sr;
+      }
+    } else {
+      st = solve_multi(c, fj, uj, lj, nb, &bi, as_stream(stream));
+    }
     agg.iters = std::max(agg.iters, bi.iters);
     agg.relres_est = std::max(agg.relres_est, bi.relres_est);
     agg.relres_true = std::max(agg.relres_true, bi.relres_true);
@@ -97,6 +117,7 @@ afi_status ieti_solve_adjoint(afi_ctx *c, const double *g, double *z, double *zl
 afi_status afi_lame_grad(afi_ctx *c, const double *u, const double *z, double *grad, void *stream) {
   if (!c || !u || !z || !grad) { set_error("afi_lame_grad: invalid argument"); return AFI_EINVAL; }
   if (!has_operator(c)) return AFI_EINVAL;
+  if (c->mf) { set_error("afi_lame_grad: not available with AFI_VARIANT_MATRIX_FREE"); return AFI_EINVAL; }
   return op_lame_grad(c, u, z, grad, as_stream(stream));
 }
 

@@ -511,6 +511,7 @@ __global__ void k_lame_final(const double *partial, int nblk, int npatch, double
 }
 
 afi_status op_load(afi_ctx *c, const double *coef, double *f, cudaStream_t s) {
+  if (c->mf) return mf_mass(c, coef, f, s);
   const int D = c->dim;
   int maxNQ = 1, maxN = 1;
   for (auto &p : c->hp) { maxNQ = std::max(maxNQ, p.NQ); maxN = std::max(maxN, p.N); }

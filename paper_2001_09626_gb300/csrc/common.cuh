@@ -204,6 +204,16 @@ struct afi_ctx {
   long long *ex_koff = nullptr, *ex_aoff = nullptr;  // their per-patch offsets
   bool mv_exact = false;                      // apply the FP64 stencil even if pairs exist
   double *qgeo = nullptr; long long nqp = 0;  // [DIM*DIM + 1][nqp] SoA
+  // matrix-free stiffness and mass (AFI_VARIANT_MATRIX_FREE, mf.cu)
+  bool mf = false;
+  int mf_p = 0;                               // the common degree
+  long long mf_ne = 0;                        // elements of all patches
+  long long *mf_eoff = nullptr;               // [npatch + 1] first element of each patch
+  float *mf_ctrlf = nullptr;                  // FP32 control points, patch-relative
+  float *mf_xf = nullptr, *mf_yf = nullptr;   // FP32 input and sums of the FP32 form
+  int mf_grid[4] = {0, 0, 0, 0};              // [fp32 / fp64 stiffness, fp32 / fp64 mass]
+  int mf_wpc[4] = {0, 0, 0, 0};
+  int mf_smem[4] = {0, 0, 0, 0};
   // geometry-inclusion local solvers (AFI_VARIANT_GEO, Section 5.2.3)
   bool geo = false;
   int nbase_tab = 0;                          // tables before the per-(patch, component) ones
@@ -305,6 +315,10 @@ afi_status op_stiffness_fp64(afi_ctx *c, const double *x, double *y, cudaStream_
 afi_status op_stiffness_multi(afi_ctx *c, const double *x, long long xstride, double *y,
                               long long ystride, int nr, cudaStream_t s);
 afi_status stiffness_multi_prepare(afi_ctx *c, cudaStream_t s);
+// mf.cu (matrix-free stiffness and mass)
+afi_status mf_setup(afi_ctx *c);
+afi_status mf_stiffness(afi_ctx *c, const double *x, double *y, bool exact, cudaStream_t s);
+afi_status mf_mass(afi_ctx *c, const double *coef, double *f, cudaStream_t s);
 afi_status solve_multi(afi_ctx *c, const double *f, double *u, double *lam, int nr,
                        afi_info *info, cudaStream_t s);
 // exact.cu (EXACT local solvers, Section 5.1)

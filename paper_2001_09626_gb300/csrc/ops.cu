@@ -1221,6 +1221,41 @@ static afi_status fp64_restart(afi_ctx *c, const MinresBufs &M, double bnorm, Lo
   return AFI_OK;
 }
 
+// Iterative refinement of the matrix-free FP32 form (AFI_VARIANT_MATRIX_FREE
+// without AFI_VARIANT_STENCIL_F64): each MINRES run on b' = b - calA x (FP32
+// products) stops once its estimate has fallen by kRefineDrop or reached
+// the tolerance, takes one FP64 true residual, and the next run solves for
+// the correction from x; at most kRefineMax runs after the first.
+constexpr double kRefineDrop = 1e-4;
+constexpr int kRefineMax = 12;
+
+static bool refines(const afi_ctx *c) {
+  return c->mf && !(c->opt.variant & AFI_VARIANT_STENCIL_F64);
+}
+
+// one refinement run from the iterate in M.x, whose residual b - calA x is
+// in M.tmp: x0 = x, solve calA d = b - calA x0, x = x0 + d; R is replaced by
+// the run's result and its iterations are added to *iters
+static afi_status refine_restart(afi_ctx *c, const MinresBufs &M, double bnorm, bool use_graph,
+                                 LoopResult &R, long *iters, cudaStream_t s) {
+  const long nt = c->n_dof + c->n_c;
+  double *hs = c->host_small;
+  AFI_CUDA(cudaMemcpyAsync(M.x0, M.x, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  AFI_CUDA(cudaMemcpyAsync(M.b, M.tmp, nt * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  const double rnorm = R.relres_true * bnorm;
+  const double tol_est = std::max(c->opt.tol * bnorm / (rnorm > 0 ? rnorm : 1.0), kRefineDrop);
+  afi_status e = minres_start(c, M, c->small, tol_est, std::max(1L, (long)c->opt.maxit - *iters), hs, s);
+  if (e == AFI_OK) {
+    R = minres_loop(c, M, c->small, use_graph, bnorm, true, true, hs, s);
+    *iters += (long)hs[S_ITN];
+  } else {
+    R.status = e;
+  }
+  launch(k_add, nblk(nt), 256, 0, s, (const double *)M.x0, (const double *)M.x, M.x, nt);
+  AFI_LAUNCH_CHECK();
+  return AFI_OK;
+}
+
 // one right-hand side
 afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, afi_info *info,
                      cudaStream_t s) {
@@ -1233,7 +1268,8 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
   AFI_TRY(rhs_setup(c, M, f, s));
   double *hs = c->host_small;
   const double tol = c->opt.tol;
-  AFI_TRY(minres_start(c, M, c->small, tol, c->opt.maxit, hs, s));
+  const bool refine = refines(c);
+  AFI_TRY(minres_start(c, M, c->small, refine ? std::max(tol, kRefineDrop) : tol, c->opt.maxit, hs, s));
   const double bnorm = sqrt(hs[S_BNORM2]);
   const bool use_graph = c->opt.use_graph != 0;
   if (use_graph) {
@@ -1241,11 +1277,18 @@ afi_status solve_one(afi_ctx *c, const double *f, double *u, double *lam_out, af
     AFI_TRY(ensure_graph(c, M));
   }
   const bool pairs = stiffness_has_pairs(c);
-  LoopResult R = minres_loop(c, M, c->small, use_graph, bnorm, pairs,
-                             pairs && (c->opt.variant & AFI_VARIANT_FORCE_RESTART), hs, s);
+  LoopResult R = minres_loop(c, M, c->small, use_graph, bnorm, pairs || refine,
+                             refine || (pairs && (c->opt.variant & AFI_VARIANT_FORCE_RESTART)), hs, s);
   long iters = (long)hs[S_ITN];
   int restarts = 0;
-  if (R.status == AFI_OK && R.stalled) {
+  if (refine) {
+    while (R.status == AFI_OK && R.stalled && R.relres_true > tol && restarts < kRefineMax &&
+           iters < (long)c->opt.maxit) {
+      AFI_TRY(refine_restart(c, M, bnorm, use_graph, R, &iters, s));
+      ++restarts;
+    }
+    if (R.status == AFI_OK && R.relres_true > tol) R.status = AFI_ENOT_CONVERGED;
+  } else if (R.status == AFI_OK && R.stalled) {
     AFI_TRY(fp64_restart(c, M, bnorm, R, &iters, s));
     restarts = 1;
   }

@@ -185,6 +185,12 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
               "AFI_VARIANT_EXACT");
     return AFI_EINVAL;
   }
+  if ((opt->variant & AFI_VARIANT_MATRIX_FREE) &&
+      (opt->variant & (AFI_VARIANT_LOCAL_ONLY | AFI_VARIANT_EXACT | AFI_VARIANT_GEO))) {
+    set_error("AFI_VARIANT_MATRIX_FREE excludes AFI_VARIANT_LOCAL_ONLY, AFI_VARIANT_EXACT and "
+              "AFI_VARIANT_GEO");
+    return AFI_EINVAL;
+  }
   c->dim = D;
   c->npatch = NP;
   c->geo = (opt->variant & AFI_VARIANT_GEO) != 0;
@@ -343,7 +349,12 @@ afi_status setup_context(const afi_problem *prob, const afi_options *opt, afi_ct
     P.lscale = c->geo ? 1.0 : P.Hs;
   }
   AFI_CUDA(cudaMemcpy(c->patches, c->hp.data(), NP * sizeof(DevPatch), cudaMemcpyHostToDevice));
-  if (!(opt->variant & AFI_VARIANT_LOCAL_ONLY)) {
+  if (opt->variant & AFI_VARIANT_MATRIX_FREE) {
+    c->nqp = 0;
+    c->stencil_n = 0;
+    c->stencil2_n = 0;
+    AFI_TRY(mf_setup(c));
+  } else if (!(opt->variant & AFI_VARIANT_LOCAL_ONLY)) {
     AFI_TRY(dalloc(c, (void **)&c->qgeo, (size_t)(D * D + 1) * qoff * sizeof(double)));
     AFI_TRY(compute_geometry(c));
     AFI_TRY(dalloc(c, (void **)&c->stencil, (size_t)soff * sizeof(double)));
@@ -617,7 +628,7 @@ void free_context(afi_ctx *c) {
                   c->nest_gc, c->pn_ptr, c->pn_ent, c->nest_tmp, c->tcsplit[0][0].d_pbounds,
                   c->tcsplit[0][0].d_lbounds, c->tcsplit[0][1].d_pbounds, c->tcsplit[0][1].d_lbounds,
                   c->tcsplit[1][0].d_pbounds, c->tcsplit[1][0].d_lbounds, c->tcsplit[1][1].d_pbounds,
-                  c->tcsplit[1][1].d_lbounds};
+                  c->tcsplit[1][1].d_lbounds, c->mf_eoff, c->mf_ctrlf, c->mf_xf, c->mf_yf};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (c->host_small) cudaFreeHost(c->host_small);

@@ -590,6 +590,8 @@ afi_status op_stiffness_multi(afi_ctx *c, const double *x, long long xstride, do
 }
 
 afi_status op_stiffness(afi_ctx *c, const double *x, double *y, cudaStream_t s) {
+  if (c->mf)
+    return mf_stiffness(c, x, y, c->mv_exact || (c->opt.variant & AFI_VARIANT_STENCIL_F64), s);
   if (c->stencil2 && !c->mv_exact) {
     afi_status st = AFI_OK;
     if (rows_dispatch(c, x, 0, y, 0, 1, s, false, &st)) return st;

@@ -15,7 +15,7 @@ from . import afieti as _a
 class Solver:
     def __init__(self, problem, prec="fp64", tol=1e-8, maxit=2000, device=None, use_graph=False,
                  local_only=False, fd_slab=False, stencil_f64=False, force_restart=False,
-                 exact=False, geo=False, fd_fixed=False):
+                 exact=False, geo=False, fd_fixed=False, matrix_free=False):
         if not torch.cuda.is_available():
             raise RuntimeError("libafieti needs a CUDA device")
         self.device = torch.device(device or "cuda")
@@ -30,7 +30,8 @@ class Solver:
                                         | (_a.AFI_VARIANT_FORCE_RESTART if force_restart else 0)
                                         | (_a.AFI_VARIANT_EXACT if exact else 0)
                                         | (_a.AFI_VARIANT_GEO if geo else 0)
-                                        | (_a.AFI_VARIANT_FD_FIXED if fd_fixed else 0))
+                                        | (_a.AFI_VARIANT_FD_FIXED if fd_fixed else 0)
+                                        | (_a.AFI_VARIANT_MATRIX_FREE if matrix_free else 0))
         self.n_dof, self.n_c = _a.afi_sizes(self.ctx)
         self.last_info = None
 
