@@ -56,9 +56,65 @@ __device__ __forceinline__ void mf_tabs(const T *tb, int dir, T (&v)[NB][NB], T 
     }
 }
 
+// patch and element coordinates of element ge (eoff[k] <= ge < eoff[k + 1])
+template <int P>
+__device__ __forceinline__ int mf_locate(const DevPatch *__restrict__ Pp,
+                                         const long long *__restrict__ eoff, int npatch,
+                                         long long ge, int (&e)[3]) {
+  int lo = 0, hi = npatch - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (eoff[mid] <= ge) lo = mid; else hi = mid - 1;
+  }
+  const int ne1 = Pp[lo].n[0] - P, ne2 = Pp[lo].n[1] - P;
+  const long long le = ge - eoff[lo];
+  e[0] = (int)(le % ne1);
+  e[1] = (int)((le / ne1) % ne2);
+  e[2] = (int)(le / ((long long)ne1 * ne2));
+  return lo;
+}
+
+// one element's tables (tv, entries lane + 32 j of tb's layout) and fields
+// (fv, entries lane + 32 j of [f][t3][t2][t1]: f = 0..2 control-point
+// coordinates, 3..5 x) into registers
+template <typename T, int P, int NT, int NF>
+__device__ __forceinline__ void mf_fetch(const DevPatch &pt, const Tab1D *__restrict__ tabs,
+                                         const T *__restrict__ pool, const T *__restrict__ ctrl,
+                                         const T *__restrict__ x, const int (&e)[3], int lane,
+                                         T (&tv)[NT], T (&fv)[NF]) {
+  constexpr int NB = P + 1, NB2 = NB * NB, NB3 = NB2 * NB;
+#pragma unroll
+  for (int j = 0; j < NT; ++j) {
+    const int i = lane + 32 * j;
+    if (i < 6 * NB2) {
+      const int dir = i / (2 * NB2), rem = i - dir * 2 * NB2, vd = rem / NB2, gt = rem - vd * NB2;
+      const Tab1D &Tt = tabs[pt.tab[dir]];
+      tv[j] = pool[(vd ? Tt.der : Tt.val) + (long long)e[dir] * NB2 + gt];
+    } else if (i < 6 * NB2 + 3 * NB) {
+      const int jj = i - 6 * NB2, dir = jj / NB, g = jj - dir * NB;
+      tv[j] = pool[tabs[pt.tab[dir]].qw + (long long)e[dir] * NB + g];
+    }
+  }
+  const int n1 = pt.n[0], n2 = pt.n[1];
+#pragma unroll
+  for (int j = 0; j < NF; ++j) {
+    const int i = lane + 32 * j;
+    if (i < 6 * NB3) {
+      const int f = i / NB3, r = i - f * NB3;
+      const int t1 = r % NB, t2 = (r / NB) % NB, t3 = r / NB2;
+      const long long node = (e[0] + t1) + (long long)n1 * ((e[1] + t2) + (long long)n2 * (e[2] + t3));
+      fv[j] = f < 3 ? ctrl[pt.xoff + node * 3 + f] : x[pt.off + (long long)(f - 3) * pt.N + node];
+    }
+  }
+}
+
 // y += A x (MASS = false) or y += M x (MASS = true) over every element.
 // pool, ctrl, x and y are in the arithmetic type T; eoff[k] is the first
 // element of patch k (eoff[npatch] = ne).  *flag is set where det J <= 0.
+// The FP32 form fetches the warp's next element into registers while it
+// works on the current one (the element's global loads are otherwise
+// waited on at every element); the FP64 form, bound by the FP64 pipe,
+// fetches each element when it starts.
 template <typename T, int P, bool MASS>
 __global__ void __launch_bounds__(32 * kMfMaxWarps)
 k_mf(const DevPatch *__restrict__ Pp, const Tab1D *__restrict__ tabs, const T *__restrict__ pool,
@@ -71,38 +127,37 @@ k_mf(const DevPatch *__restrict__ Pp, const Tab1D *__restrict__ tabs, const T *_
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   T *tb = reinterpret_cast<T *>(mf_smem) + (size_t)wib * S::PER_WARP;
   T *R0 = tb + S::TABS, *R1 = R0 + S::REG;
+  constexpr bool PF = sizeof(T) == 4;
+  constexpr int NT = (6 * NB2 + 3 * NB + 31) / 32, NF = (6 * NB3 + 31) / 32;
+  T tv[NT], fv[NF];
   const long long nw = (long long)gridDim.x * wpc;
-  for (long long ge = (long long)blockIdx.x * wpc + wib; ge < ne; ge += nw) {
-    int lo = 0, hi = npatch - 1;   // patch k with eoff[k] <= ge < eoff[k + 1]
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (eoff[mid] <= ge) lo = mid; else hi = mid - 1;
+  long long ge = (long long)blockIdx.x * wpc + wib;
+  int en[3] = {0, 0, 0}, kn = 0;   // the fetched element
+  if (PF && ge < ne) {
+    kn = mf_locate<P>(Pp, eoff, npatch, ge, en);
+    mf_fetch<T, P, NT, NF>(Pp[kn], tabs, pool, ctrl, x, en, lane, tv, fv);
+  }
+  for (; ge < ne; ge += nw) {
+    if (!PF) {
+      kn = mf_locate<P>(Pp, eoff, npatch, ge, en);
+      mf_fetch<T, P, NT, NF>(Pp[kn], tabs, pool, ctrl, x, en, lane, tv, fv);
     }
-    const DevPatch &pt = Pp[lo];
+    const DevPatch &pt = Pp[kn];
     const int n1 = pt.n[0], n2 = pt.n[1], N = pt.N;
-    const int ne1 = n1 - P, ne2 = n2 - P;
-    const long long le = ge - eoff[lo];
-    const int e[3] = {(int)(le % ne1), (int)((le / ne1) % ne2), (int)(le / ((long long)ne1 * ne2))};
-
-    // tables of the element: tb[(2 dir + vd) NB2 + g NB + t], weights at 6 NB2
-    for (int i = lane; i < 6 * NB2 + 3 * NB; i += 32) {
-      if (i < 6 * NB2) {
-        const int dir = i / (2 * NB2), rem = i - dir * 2 * NB2, vd = rem / NB2, gt = rem - vd * NB2;
-        const Tab1D &Tt = tabs[pt.tab[dir]];
-        tb[i] = pool[(vd ? Tt.der : Tt.val) + (long long)e[dir] * NB2 + gt];
-      } else {
-        const int j = i - 6 * NB2, dir = j / NB, g = j - dir * NB;
-        tb[i] = pool[tabs[pt.tab[dir]].qw + (long long)e[dir] * NB + g];
-      }
-    }
-    // fields [f][t3][t2][t1]: f = 0..2 control-point coordinates, 3..5 x
-    for (int i = lane; i < 6 * NB3; i += 32) {
-      const int f = i / NB3, r = i - f * NB3;
-      const int t1 = r % NB, t2 = (r / NB) % NB, t3 = r / NB2;
-      const long long node = (e[0] + t1) + (long long)n1 * ((e[1] + t2) + (long long)n2 * (e[2] + t3));
-      R0[i] = f < 3 ? ctrl[pt.xoff + node * 3 + f] : x[pt.off + (long long)(f - 3) * N + node];
-    }
+    const int e[3] = {en[0], en[1], en[2]};
+    // tables of the element: tb[(2 dir + vd) NB2 + g NB + t], weights at
+    // 6 NB2; fields [f][t3][t2][t1] at R0
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+      if (lane + 32 * j < 6 * NB2 + 3 * NB) tb[lane + 32 * j] = tv[j];
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+      if (lane + 32 * j < 6 * NB3) R0[lane + 32 * j] = fv[j];
     __syncwarp();
+    if (PF && ge + nw < ne) {   // the next element's loads run during this one
+      kn = mf_locate<P>(Pp, eoff, npatch, ge + nw, en);
+      mf_fetch<T, P, NT, NF>(Pp[kn], tabs, pool, ctrl, x, en, lane, tv, fv);
+    }
 
     // pass 1 (direction 1): S1[f][vd][t3][t2][g1] at R0 + 6 NB3
     {
