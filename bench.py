@@ -10,8 +10,10 @@ x 12/24/48 x 32, nine distinct patch shapes, 6.59 M DoF), all-floating with
 Dirichlet conditions on the whole outer boundary, body force with
 uniform[-1,1] nodal coefficients (seeded), preconditioned MINRES to 1e-8
 relative residual (estimate and true residual).  `--workload C2|C4|C5-mid`
-selects another configuration (C5 itself, 1.9 TB of stored stiffness, is
-measured by `--fd-only`).
+selects another configuration.  `--workload C5` runs the metric's own
+configuration, whose stored stiffness would need 1.9 TB, on the matrix-free
+operator (run_matrix_free; about ten minutes with three warm-up solves), and
+`--fd-only --workload C5` its local solvers alone.
 
 One step = one complete AF-IETI solve (lambda_0, MINRES, recovery) with the
 load vector resident in HBM.  The per-step inputs are larger than L2: every
