@@ -52,3 +52,19 @@ def test_pair_copy_is_smaller_than_the_fp64_stencil():
         prob = W.config(name)
         flops, stored = bench.stencil_stats(prob)
         assert 8 * (flops // 2) < bench.pair_copy_bytes(prob) < stored
+
+
+def test_matrix_free_flop_count():
+    """The matrix-free kernel's FLOPs per element (bench roofline), against a
+    pass-by-pass enumeration: forward, six fields, contractions producing
+    2 / 3 / 3 outputs per line in directions 1 / 2 / 3; back, three
+    components, 3 / 3 / 2 (one output of back pass 2 takes two products);
+    each output of a line is a (p+1)-term FMA chain over (p+1)^2 lines."""
+    for p in range(1, 6):
+        nb = p + 1
+        lines = nb * nb
+        fma = 6 * lines * nb * (2 + 3 + 3) * nb + 3 * lines * nb * (3 + 3 + 2) * nb
+        pointwise = 168 * nb ** 3
+        assert bench.mf_flops_per_element(p) == 2 * fma + pointwise
+    assert bench.mf_flops_per_element(4) == 111000
+    assert abs(bench.fp32_peak_tflops(2070.0) - 80.55) < 0.01
