@@ -201,12 +201,11 @@ typedef struct {
                                       estimate has fallen by 1e-4 (or reached
                                       tol) and the next solves for the
                                       correction, at most 12 more runs
-                                      (afi_info.fp64_restarts counts them);
-                                      the true residual, afi_apply in
-                                      AFI_OP_SADDLE's residual form and, with
-                                      AFI_VARIANT_STENCIL_F64, every product
-                                      are FP64.  afi_apply(AFI_OP_STIFFNESS)
-                                      is the FP32 form unless
+                                      (afi_info.fp64_restarts counts them).
+                                      The true residual is always FP64, and
+                                      with AFI_VARIANT_STENCIL_F64 every
+                                      product is.  afi_apply(AFI_OP_STIFFNESS /
+                                      AFI_OP_SADDLE) uses the FP32 form unless
                                       AFI_VARIANT_STENCIL_F64 is set.  Several
                                       right-hand sides are solved one after
                                       the other.  Excludes
