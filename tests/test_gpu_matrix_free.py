@@ -13,7 +13,7 @@ by rounding only.
     norm for a random input.
   * Solves: the mixed form (TF32 local solvers, FP32 products refined against
     the FP64 true residual) must meet the FP64 tolerance 1e-8 on the true
-    residual and the spec solution error 1e-6; the FP64 form, 1e-10 and
+    residual and a solution error of 1e-6; the FP64 form, 1e-10 and
     1e-7 (the tolerances of the stored-stencil solves).
 The full-size rows are C5-mid's (the C5 patch: p = 4, 48^3 elements), from
 the oracle's quadrature over each sampled node's support."""
