@@ -4,12 +4,13 @@ and the preconditioned MINRES driver (Section 4, eqs. 4.6, 4.7, 4.9).
 
 The FETI subdomains are the patches, so the method shards by patch:
   * a rank owns a set of patches (their torn dofs, patch by patch in
-    increasing patch order) and the constraint rows whose first copy lies on
-    one of them.  All rows of a geometric node share that first copy, so the
-    node-wise (B B^T)^{-1} of P_S (Remark 1) never crosses ranks;
-  * B w needs, for each owned row whose second copy lives elsewhere, that
-    copy's value: a point-to-point halo of shell values;
-  * B^T chi sends the same rows' multipliers back the other way;
+    increasing patch order) and the constraint rows whose lead entry (below)
+    lies on one of them.  All rows of a geometric node share that entry, and
+    so do a nested face's rows, so the block-diagonal (B B^T)^{-1} of P_S
+    (Remark 1) never crosses ranks;
+  * B w needs, for each owned row with entries on patches owned elsewhere,
+    those dofs' values: a point-to-point halo of shell values;
+  * B^T chi sends the same rows' weighted multipliers back the other way;
   * G^T chi = R^T B^T chi is a per-patch 6-vector (3 in 2D): an all-gather,
     after which every rank applies (G^T G)^{-1} redundantly;
   * MINRES inner products are an all-reduce of per-rank partial sums.
@@ -18,13 +19,14 @@ The patch-local pieces (stiffness A^(k), the local solvers P_A^{-1}, the Schur
 block S^(k), the rigid modes R_k) come from the caller as callables acting on
 a rank's own patches; on GPUs they are the library's kernels on a context
 that holds those patches.  Exchanges use torch.distributed (NCCL across GPUs,
-gloo on CPU).  The constraint rows are the library's (dof A, dof B or -1),
-one star row u_A - u_B per additional copy of a node, or e_A for a copy on
-the Dirichlet boundary (reading 1 of the design notes).  The rows of nested
-non-conforming faces (a fine copy tied to several coarse ones with
-knot-insertion weights) are not covered: a sharded form would give each
-nested face's rows to the fine patch's owner and bring the coarse face's
-values in by the same kind of halo."""
+gloo on CPU).  The constraint rows are the library's: one star row
+u_A - u_B per additional copy of a node, or e_A for a copy on the Dirichlet
+boundary, and the rows of nested non-conforming faces, which
+tie a fine point to the coarse face's points with knot-insertion weights.
+Any row belongs to the owner of its +1 entry (the first copy, or the fine
+point), and its other entries are fetched by the halo; a nested face's rows
+thus sit with the fine patch's owner, beside their dense (B B^T)^{-1}
+block."""
 from __future__ import annotations
 
 import math
@@ -48,14 +50,45 @@ def lpt_partition(sizes, nranks):
     return owner
 
 
+def rows_csr(rows, ndof):
+    """The constraint matrix B (scipy CSR) of star and Dirichlet rows given as
+    (dof A, dof B or -1): u_A - u_B, or e_A."""
+    import scipy.sparse as sp
+    rows = np.asarray(rows, dtype=np.int64)
+    r, c, v = [], [], []
+    for i, (da, db) in enumerate(rows):
+        r.append(i)
+        c.append(int(da))
+        v.append(1.0)
+        if db >= 0:
+            r.append(i)
+            c.append(int(db))
+            v.append(-1.0)
+    return sp.csr_matrix((v, (r, c)), shape=(len(rows), int(ndof)))
+
+
 class ExchangePlan:
     """What rank `rank` owns and exchanges, built identically on every rank
-    from the global row list, the torn offsets of the patches and the owner
-    of every patch."""
+    from the global constraint rows, the torn offsets of the patches and the
+    owner of every patch.
+
+    rows is either an [n_c, 2] array (dof A, dof B or -1) of star and
+    Dirichlet rows, or the constraint matrix B itself (scipy sparse, any
+    rows).  A row belongs to the owner of its lead dof, the first entry with
+    coefficient +1: the first copy of a node, or the fine point of a nested
+    non-conforming face's row u_fine - sum_c W u_coarse.  Its other entries
+    on patches owned elsewhere are the halo."""
 
     def __init__(self, rows, offsets, owner, rank, nranks):
-        rows = np.asarray(rows, dtype=np.int64)
+        import scipy.sparse as sp
+        from scipy.sparse.csgraph import connected_components
         offsets = np.asarray(offsets, dtype=np.int64)
+        ndof = int(offsets[-1])
+        if isinstance(rows, np.ndarray) or not sp.issparse(rows):
+            B = rows_csr(rows, ndof)
+        else:
+            B = sp.csr_matrix(rows)
+        B.sort_indices()
         self.rank, self.nranks = rank, nranks
         self.owner = np.asarray(owner, dtype=np.int64)
         npatch = len(offsets) - 1
@@ -68,64 +101,79 @@ class ExchangePlan:
             n += int(offsets[k + 1] - offsets[k])
         self.n_local = n
         self.offsets = offsets
-
-        def patch_of(d):
-            return int(np.searchsorted(offsets, d, side="right") - 1)
-
-        def local(d):
-            k = patch_of(d)
-            return self.loc_off[k] + int(d - offsets[k])
-        pa = np.array([patch_of(d) for d in rows[:, 0]], dtype=np.int64)
-        pb = np.array([patch_of(d) if d >= 0 else -1 for d in rows[:, 1]], dtype=np.int64)
-        own = self.owner[pa] == rank
-        self.rows = np.nonzero(own)[0]                    # owned global rows, increasing
+        patch_of = lambda d: np.searchsorted(offsets, d, side="right") - 1
+        loc_base = np.full(npatch, -1, dtype=np.int64)
+        for k in self.patches:
+            loc_base[k] = self.loc_off[k] - offsets[k]
+        ip, ix, dv = B.indptr, B.indices.astype(np.int64), B.data
+        lead = np.empty(B.shape[0], dtype=np.int64)
+        for r in range(B.shape[0]):
+            pos = np.nonzero(dv[ip[r]:ip[r + 1]] == 1.0)[0]
+            if len(pos) == 0:
+                raise ValueError(f"constraint row {r} has no +1 entry")
+            lead[r] = ix[ip[r] + pos[0]]
+        row_owner = self.owner[patch_of(lead)]
+        self.rows = np.nonzero(row_owner == rank)[0]          # owned global rows, increasing
         self.n_rows = len(self.rows)
-        self.a_loc = np.array([local(d) for d in rows[self.rows, 0]], dtype=np.int64)
-        # second copies: local, remote (halo) or none (Dirichlet row)
-        self.b_loc = np.full(self.n_rows, -1, dtype=np.int64)
-        self.halo_in = {}    # peer -> (positions among owned rows, peer's local dofs)
+        # entries of the owned rows: local (position, local dof, weight) and,
+        # per peer, (position, slot among the peer's distinct dofs, weight)
+        lp, ld, lw = [], [], []
+        rem = {}
         for i, r in enumerate(self.rows):
-            if rows[r, 1] < 0:
-                continue
-            q = int(self.owner[pb[r]])
-            if q == rank:
-                self.b_loc[i] = local(rows[r, 1])
-            else:
-                self.halo_in.setdefault(q, ([], []))
-                self.halo_in[q][0].append(i)
-                self.halo_in[q][1].append(int(rows[r, 1]))
-        # rows owned elsewhere whose second copy is here: we send those copies'
-        # values for B w and receive those rows' multipliers for B^T chi
-        self.halo_out = {}   # peer -> local dofs (in the peer's row order)
-        for r in np.nonzero(~own)[0]:
-            if rows[r, 1] < 0 or self.owner[pb[r]] != rank:
-                continue
-            q = int(self.owner[pa[r]])
-            self.halo_out.setdefault(q, []).append(local(rows[r, 1]))
-        # (positions among the owned rows, global second copies), in increasing
-        # row order on both sides of each exchange
-        self.halo_in = {q: (np.array(p, dtype=np.int64), np.array(d, dtype=np.int64))
-                        for q, (p, d) in self.halo_in.items()}
-        self.halo_out = {q: np.array(v, dtype=np.int64) for q, v in self.halo_out.items()}
-        # node groups of the owned star rows (consecutive rows sharing a first
-        # copy) for the node-wise (B B^T)^{-1} = I - 1 1^T / m on each star
-        self.groups = []
-        i = 0
-        while i < self.n_rows:
-            j = i + 1
-            if self.b_loc[i] >= 0 or i in self._halo_positions():
-                while (j < self.n_rows and rows[self.rows[j], 0] == rows[self.rows[i], 0]
-                       and rows[self.rows[j], 1] >= 0):
-                    j += 1
-                self.groups.append((i, j))
-            i = j
-
-    def _halo_positions(self):
-        if not hasattr(self, "_hp"):
-            self._hp = set()
-            for p, _ in self.halo_in.values():
-                self._hp.update(int(x) for x in p)
-        return self._hp
+            for e in range(ip[r], ip[r + 1]):
+                d = int(ix[e])
+                k = int(patch_of(d))
+                q = int(self.owner[k])
+                if q == rank:
+                    lp.append(i)
+                    ld.append(int(loc_base[k] + d))
+                    lw.append(float(dv[e]))
+                else:
+                    rem.setdefault(q, []).append((i, d, float(dv[e])))
+        self.loc_pos = np.array(lp, dtype=np.int64)
+        self.loc_dof = np.array(ld, dtype=np.int64)
+        self.loc_w = np.array(lw, dtype=np.float64)
+        self.halo_in = {}    # peer -> (positions, slots, weights); the peer sends sorted dofs
+        for q, ent in rem.items():
+            dofs = np.unique(np.array([d for _, d, _ in ent], dtype=np.int64))
+            slot = {int(d): j for j, d in enumerate(dofs)}
+            self.halo_in[q] = (np.array([i for i, _, _ in ent], dtype=np.int64),
+                               np.array([slot[d] for _, d, _ in ent], dtype=np.int64),
+                               np.array([w for _, _, w in ent], dtype=np.float64), len(dofs))
+        # rows owned elsewhere with entries on my patches: I send those dofs'
+        # values for B w and receive their B^T contributions, in increasing
+        # global dof order on both sides
+        self.halo_out = {}   # peer -> my local dofs
+        mine = np.zeros(npatch, dtype=bool)
+        mine[self.patches] = True
+        for r in np.nonzero(row_owner != rank)[0]:
+            q = int(row_owner[r])
+            for e in range(ip[r], ip[r + 1]):
+                d = int(ix[e])
+                k = int(patch_of(d))
+                if mine[k]:
+                    self.halo_out.setdefault(q, set()).add(d)
+        self.halo_out = {q: np.array([int(loc_base[patch_of(d)] + d) for d in sorted(v)],
+                                     dtype=np.int64) for q, v in self.halo_out.items()}
+        # (B B^T)^{-1} of the owned rows: block diagonal over the connected
+        # components of rows sharing a dof (a node's star; a nested face's
+        # rows per component).  A component must not reach rows owned
+        # elsewhere, which holds when every row touching a dof of an owned
+        # row is owned here.
+        Bo = B[self.rows]
+        M = (Bo @ B.T).tocsr()
+        if self.n_rows and np.any(row_owner[M.nonzero()[1]] != rank):
+            raise ValueError("B B^T couples rows of two ranks: the node-wise block inverse "
+                             "would cross ranks")
+        Mo = (Bo @ Bo.T).tocsr()
+        nb, lab = connected_components(Mo, directed=False) if self.n_rows else (0, np.zeros(0, int))
+        self.blocks = []     # (positions, dense inverse of the block of B B^T)
+        order = np.argsort(lab, kind="stable")
+        starts = np.searchsorted(lab[order], np.arange(nb + 1))
+        for b in range(nb):
+            pos = order[starts[b]:starts[b + 1]]
+            blk = Mo[pos][:, pos].toarray()
+            self.blocks.append((pos, np.linalg.inv(blk)))
 
 
 def _exchange(send, recv_shapes, dtype, device):
@@ -165,28 +213,30 @@ class DistributedAFIETI:
     def B(self, w):
         """Owned rows of B w."""
         p = self.p
-        out = w[torch.as_tensor(p.a_loc)].clone()
-        bl = torch.as_tensor(p.b_loc)
-        m = bl >= 0
-        out[m] -= w[bl[m]]
+        out = torch.zeros(p.n_rows, dtype=w.dtype, device=w.device)
+        out.index_add_(0, torch.as_tensor(p.loc_pos),
+                       torch.as_tensor(p.loc_w) * w[torch.as_tensor(p.loc_dof)])
         send = {q: w[torch.as_tensor(d)] for q, d in p.halo_out.items()}
-        got = _exchange(send, {q: len(v[0]) for q, v in p.halo_in.items()}, w.dtype, w.device)
-        for q, (pos, _) in p.halo_in.items():
-            out[torch.as_tensor(pos)] -= got[q]
+        got = _exchange(send, {q: v[3] for q, v in p.halo_in.items()}, w.dtype, w.device)
+        for q, (pos, slot, wt, _) in p.halo_in.items():
+            out.index_add_(0, torch.as_tensor(pos), torch.as_tensor(wt) * got[q][torch.as_tensor(slot)])
         return out
 
     def Bt(self, chi):
-        """B^T chi on the rank's own dofs, from its owned rows' multipliers."""
+        """B^T chi on the rank's own dofs, from its owned rows' multipliers and
+        the contributions of rows owned elsewhere."""
         p = self.p
         w = torch.zeros(p.n_local, dtype=chi.dtype, device=chi.device)
-        w.index_add_(0, torch.as_tensor(p.a_loc), chi)
-        bl = torch.as_tensor(p.b_loc)
-        m = bl >= 0
-        w.index_add_(0, bl[m], -chi[m])
-        send = {q: chi[torch.as_tensor(pos)] for q, (pos, _) in p.halo_in.items()}
+        w.index_add_(0, torch.as_tensor(p.loc_dof),
+                     torch.as_tensor(p.loc_w) * chi[torch.as_tensor(p.loc_pos)])
+        send = {}
+        for q, (pos, slot, wt, nd) in p.halo_in.items():
+            c = torch.zeros(nd, dtype=chi.dtype, device=chi.device)
+            c.index_add_(0, torch.as_tensor(slot), torch.as_tensor(wt) * chi[torch.as_tensor(pos)])
+            send[q] = c
         got = _exchange(send, {q: len(d) for q, d in p.halo_out.items()}, chi.dtype, chi.device)
         for q, d in p.halo_out.items():
-            w.index_add_(0, torch.as_tensor(d), -got[q])
+            w.index_add_(0, torch.as_tensor(d), got[q])
         return w
 
     def dot(self, a, b):
@@ -221,12 +271,13 @@ class DistributedAFIETI:
         return w - self.ops.R(y)
 
     def BBt_inv(self, chi):
-        """Node-wise (B B^T)^{-1}: identity on Dirichlet rows, I - 1 1^T / m on
-        each star of m - 1 rows (Remark 1)."""
+        """(B B^T)^{-1} on the owned rows, block by block (Remark 1): on a
+        node's star it is I - 1 1^T / m, on a nested face's rows the dense
+        inverse of their block."""
         out = chi.clone()
-        for a, b in self.p.groups:
-            m = b - a + 1
-            out[a:b] = chi[a:b] - chi[a:b].sum() / m
+        for pos, inv in self.p.blocks:
+            pt = torch.as_tensor(pos)
+            out[pt] = torch.as_tensor(inv, dtype=chi.dtype, device=chi.device) @ chi[pt]
         return out
 
     def PS(self, chi):

@@ -1,16 +1,18 @@
 """The patch-sharded design on the CPU: two gloo ranks (127.0.0.1) split the
-patches of C1 (2D) and C2-small (3D) by the LPT partition, build the exchange
-plan from the constraint rows, and run the distributed operators and MINRES
-with the oracle's patch-local pieces (stiffness, local solvers, Schur block,
-rigid modes) standing in for a rank's GPU context.
+patches of C1 (2D), C2-small (3D) and the nested non-conforming boxes
+NC-small (2D) and NC3-small (3D) by the LPT partition, build the exchange
+plan from the constraint rows (the (dof A, dof B) list, or B itself where
+nested faces add rows with knot-insertion weights), and run the distributed
+operators and MINRES with the oracle's patch-local pieces (stiffness, local
+solvers, Schur block, rigid modes) standing in for a rank's GPU context.
 
 Checked on every rank against the oracle's global operators on the same
-vectors: B w exactly, B^T chi and P_chi to rounding.  Then the whole solve:
-the same iteration count as the oracle's single-process MINRES, the same
-preconditioned-residual estimate at every iteration while it is above 1e-6
-(to 1e-10 relative; the partial sums are added in another order, which shows
-only in the last few iterations near 1e-10), and the conforming direct
-solution within 1e-8 on every patch."""
+vectors: B w exactly (to rounding for nested rows), B^T chi and P_chi to
+rounding.  Then the whole solve: the same iteration count as the oracle's
+single-process MINRES, the same preconditioned-residual estimate at every
+iteration while it is above 1e-6 (1e-4 for the nested boxes; to 1e-10
+relative, see HIST_LEVEL), and the conforming direct solution within 1e-8
+on every patch."""
 import os
 import socket
 
@@ -74,6 +76,16 @@ class _OracleLocal:
         return torch.from_numpy(self.Rloc @ y.reshape(-1).numpy())
 
 
+# The two runs add their partial sums in different orders, so the Lanczos
+# recurrences start 1e-16 apart; once Ritz values converge the recurrence
+# amplifies such differences (loss of orthogonality), at a rate set by the
+# spectrum.  The estimates are compared while they are above a level where
+# the amplified difference is still below 1e-10: 1e-6 for the conforming
+# problems, 1e-4 for the nested boxes (NC3-small drifts from about 2e-5 on,
+# with the same stopping iteration).
+HIST_LEVEL = {"C1": 1e-6, "C2-small": 1e-6, "NC-small": 1e-4, "NC3-small": 1e-4}
+
+
 def _worker(rank, world, port, name, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     import torch.distributed as dist
@@ -84,7 +96,8 @@ def _worker(rank, world, port, name, q):
     try:
         prob = W.config(name)
         orc = AFIETI(prob)
-        rows = _rows_from_B(orc.B.tocsr())
+        # conforming problems: the (dof A, dof B) row list; nested faces: B
+        rows = orc.B.tocsr() if orc.nested_faces else _rows_from_B(orc.B.tocsr())
         sizes = [orc.off[k + 1] - orc.off[k] for k in range(orc.np)]
         owner = shard.lpt_partition(sizes, world)
         plan = shard.ExchangePlan(rows, orc.off, owner, rank, world)
@@ -96,7 +109,11 @@ def _worker(rank, world, port, name, q):
         wl = torch.from_numpy(w[loc.idx].copy())
         cl = torch.from_numpy(lam[plan.rows].copy())
         bw = D.B(wl).numpy()
-        ok_B = np.array_equal(bw, (orc.B @ w)[plan.rows])
+        refB = (orc.B @ w)[plan.rows]
+        # star rows exactly; nested rows sum their entries in another order
+        ok_B = (np.array_equal(bw, refB) if not orc.nested_faces
+                else float(np.abs(bw - refB).max()) <= 1e-14 * float(np.abs(refB).max()))
+        n_remote = sum(len(v[0]) for v in plan.halo_in.values())
         btl = D.Bt(cl).numpy()
         err_Bt = float(np.abs(btl - (orc.B.T @ lam)[loc.idx]).max())
         pc = D.Pchi(cl).numpy()
@@ -116,14 +133,14 @@ def _worker(rank, world, port, name, q):
         n = min(len(hist), len(oh))
         hh = np.array(hist[:n])
         errs = np.abs(hh - oh[:n]) / oh[:n]
-        err_h = float(errs[oh[:n] > 1e-6].max())
+        err_h = float(errs[oh[:n] > HIST_LEVEL[name]].max())
         q.put((rank, ok_B, err_Bt, err_P, its, oinfo["iters"], err_u, len(plan.patches),
-               len(plan.rows), err_h))
+               len(plan.rows), err_h, n_remote))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name", ["C1", "C2-small"])
+@pytest.mark.parametrize("name", ["C1", "C2-small", "NC-small", "NC3-small"])
 def test_two_ranks_reproduce_the_single_process_solve(name):
     import torch.multiprocessing as mp
     ctx = mp.get_context("spawn")
@@ -140,7 +157,8 @@ def test_two_ranks_reproduce_the_single_process_solve(name):
     import afi_workloads as W
     orc = AFIETI(W.config(name))
     assert sum(r[7] for r in res) == orc.np and sum(r[8] for r in res) == orc.nc
-    for rank, ok_B, err_Bt, err_P, its, oits, err_u, _, _, err_h in res:
+    assert sum(r[10] for r in res) > 0      # some rows reach across the ranks
+    for rank, ok_B, err_Bt, err_P, its, oits, err_u, _, _, err_h, _ in res:
         assert ok_B, rank
         assert err_Bt <= 1e-15, (rank, err_Bt)
         assert err_P <= 1e-12, (rank, err_P)
