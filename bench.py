@@ -552,6 +552,17 @@ def run_ours(args):
     except A.AfiError as e:
         geometry_inclusion = {"skipped": str(e)}
 
+    # ---- 4. the metric's own configuration, C5 (108 M DoF, stored stencil
+    # 1.9 TB), on the matrix-free stiffness: its products and a bounded run of
+    # the mixed iterations (the full solve is `--workload C5`)
+    matrix_free_c5 = None
+    if world == 1 and args.workload == "C3":
+        try:
+            matrix_free_c5 = matrix_free_probe(args, timed)
+        except Exception as e:   # a failure here must not lose the headline line
+            matrix_free_c5 = {"skipped": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+
     multi_rhs = {"nrhs": 8, "solve_s": round((ms_multi + fd_setup_ms) / 1e3, 4),
                  "per_rhs_s": round((ms_multi / 8 + fd_setup_ms) / 1e3, 4),
                  "iterations_max": info_multi["iters"], "relres_true_max": info_multi["relres_true"],
@@ -629,6 +640,8 @@ def run_ours(args):
                     "h2d_bytes_per_step": 8 * n_dof, "d2h_bytes_per_step": 8 * n_dof},
             "gpu_launches": int(launches), "roofline": roofline, "roofline_fd": roofline_fd,
             "clocks": clocks}
+    if matrix_free_c5 is not None:
+        line["matrix_free_C5"] = matrix_free_c5
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per, det = oracle_sample_time(args.workload, steps=1, warmup=0)
         line["cpu_baseline"] = {"value": det["projection_s"], "unit": "s", "cores": det["cores"],
@@ -724,6 +737,59 @@ def fp32_peak_tflops(sm_mhz=2070.0, sms=152):
     """FP32 FMA peak from the unit counts: 128 FP32 lanes per SM, 2 FLOPs
     per FMA, at the given SM clock."""
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def matrix_free_probe(args, timed, iters=12):
+    """C5 on the matrix-free stiffness, within the default run's budget: the
+    FP32 and FP64 products (the FP32 one against the FP32 rate from the unit
+    counts) and a bounded run of `iters` mixed MINRES iterations, whose time
+    less its final FP64 true residual gives the time per iteration."""
+    import numpy as np
+    import torch
+    import afi_workloads as W
+    from paper_2001_09626_gb300 import afieti as A
+    from paper_2001_09626_gb300.solver import Solver
+    prob = W.config("C5")
+    p = int(prob.degree[0])
+    ne = sum(int(np.prod(prob.nel[k])) for k in range(prob.npatch))
+    t0 = time.time()
+    s = Solver(prob, prec=args.prec, tol=1e-8, maxit=iters, use_graph=True, matrix_free=True)
+    torch.cuda.synchronize()
+    setup_s = time.time() - t0
+    try:
+        x = torch.rand(s.n_dof, dtype=torch.float64, device="cuda")
+        s.apply(A.AFI_OP_STIFFNESS, x)
+        mv_ms = timed(lambda: s.apply(A.AFI_OP_STIFFNESS, x), 3)
+        f = s.load_vector(W.body_force_coeffs(prob))
+        s.solve(f, allow_not_converged=True)
+        ms_run = timed(lambda: s.solve(f, allow_not_converged=True), 1)
+        info = dict(s.last_info)
+    finally:
+        s.close()
+    torch.cuda.empty_cache()
+    s64 = Solver(prob, prec="fp64", tol=1e-8, maxit=iters, matrix_free=True, stencil_f64=True)
+    try:
+        x = torch.rand(s64.n_dof, dtype=torch.float64, device="cuda")
+        mv64_ms = timed(lambda: s64.apply(A.AFI_OP_STIFFNESS, x), 1)
+    finally:
+        s64.close()
+    flops = mf_flops_per_element(p) * ne
+    peak = fp32_peak_tflops(2070.0)
+    achieved = flops / (mv_ms * 1e-3) / 1e12
+    return {"workload": workload_label("C5"), "n_dof": int(prob.ndof), "setup_s": round(setup_s, 2),
+            "fp32_product_ms": round(mv_ms, 2), "fp64_product_ms": round(mv64_ms, 1),
+            "bounded_run": {"iterations": info["iters"], "ms": round(ms_run, 1),
+                            "per_iteration_ms": round(max(0.0, info["t_solve_ms"] - mv64_ms)
+                                                      / max(1, info["iters"]), 2),
+                            "method": "mixed MINRES (TF32 local solvers, FP32 products, CUDA "
+                                      "graph) capped at the iteration count, less its final "
+                                      "FP64 true residual; the full solve is bench.py "
+                                      "--workload C5"},
+            "roofline": {"bound": "alu", "kernel": f"k_mf<float,{p}>", "achieved": round(achieved, 2),
+                         "peak": round(peak, 2), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                         "peak_source": "FP32 FMA peak from the unit counts (152 SMs x 128 lanes "
+                                        "x 2 FLOP x 2070 MHz), not measured",
+                         "flops_per_launch": flops, "traffic": None}}
 
 
 def run_matrix_free(args):
