@@ -27,8 +27,10 @@ reported as setup_s.
 Beside the headline the line reports the plain FP64 form (FP64 local solvers
 and FP64 stencil), the mixed form with the FP64 stencil, eight right-hand
 sides solved together (multi_rhs), the geometry-inclusion local solvers of
-Section 5.2.3 on the same problem (geometry_inclusion), FD-apply rates and
-the rooflines of the dominant kernels.  The contexts are built one after the
+Section 5.2.3 on the same problem (geometry_inclusion), FD-apply rates, the
+rooflines of the dominant kernels, and the metric's own configuration C5 on
+the matrix-free stiffness (matrix_free_C5: its products and a bounded run of
+its iterations).  The contexts are built one after the
 other, each freed before the next, so that the largest workload fits.
 
   python bench.py [--gpus N --steps K --warmup W --prec fp32|fp64|tf32|bf16 --workload C2]
